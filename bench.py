@@ -1,0 +1,395 @@
+#!/usr/bin/env python
+"""Laminographic FBP throughput on GB300: Fourier form vs direct form.
+
+Workload (default): 512x512x256 slab, 720 projections over 360 degrees,
+detector 256 rows x 768 columns, tilt 20 degrees, 200 random ellipsoids with
+densities U[0,1], float32 projections with 1% Gaussian noise, Shepp-Logan
+filter. Inputs are seeded and synthetic (paper_2401_11101_gb300.inputs).
+
+One step = one pass of the whole hot path over the HBM-resident projections:
+  Fourier FBP: filter fused into the row FFT, column FFT (half spectrum),
+               Gaussian gridding + x1 inverse FFT, x2 inverse FFT, x3 USFFT;
+  direct FBP:  row filter, TMA-staged bilinear backprojection.
+`value` is the Fourier-form FBP throughput in GVox/s (the volume size over the
+Fourier part of the step); the direct form's figure is reported beside it.
+
+Usage: python bench.py [--gpus N --steps K --warmup W] [--impl reference]
+Multi-GPU (torchrun): every rank reconstructs its own slab (independent
+problems, no collective on the data path): weak scaling.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+import numpy as np
+import torch
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+from paper_2401_11101_gb300 import inputs as I  # noqa: E402
+
+METRIC = "lamino FBP GVox/s, Fourier vs direct on 1 GB300 @relL2<=1e-3; serve p50/p99 ms"
+WORKLOADS = {
+    "c2": "512x512x256 slab, 720 projections over 360 deg, detector 256x768, tilt 20 deg, "
+          "200 random ellipsoids rho~U[0,1], float32 projections + 1% noise, Shepp-Logan",
+    "c1": "64^3, 64 projections over 360 deg, detector 64x96, tilt 20 deg, 12 Gaussian blobs, "
+          "1% noise, Shepp-Logan",
+    "c4": "256x256x128, 400 projections over 360 deg, detector 128x384, tilt 30 deg, Gaussian "
+          "blobs, 0.5% noise, Shepp-Logan",
+}
+FP32_LANES_PER_SM = 128
+N_SMS = 152
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default="c2", choices=sorted(WORKLOADS))
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--cpu-columns", type=int, default=32)
+    return ap.parse_args()
+
+
+# --------------------------------------------------------------------- utils
+
+def dist_env():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+def measured_peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(path):
+        with open(path) as f:
+            return json.load(f), "measured"
+    return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "sm_max_mhz": 2070.0}, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi sampling of SM clocks and throttle reasons during the timed region."""
+
+    Q = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.proc = None
+        self.path = os.path.join("/tmp", f"lamino_clocks_{os.getpid()}.csv")
+
+    def start(self):
+        try:
+            self.f = open(self.path, "w")
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--query-gpu={self.Q}", "--format=csv,noheader,nounits",
+                 "-i", str(self.index), "-lms", "200"], stdout=self.f, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        time.sleep(0.25)
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        self.f.close()
+        rows = []
+        for line in open(self.path):
+            parts = [x.strip() for x in line.split(",")]
+            if len(parts) < 8:
+                continue
+            try:
+                rows.append((float(parts[0]), float(parts[1]), parts[4:8]))
+            except ValueError:
+                continue
+        os.unlink(self.path)
+        if not rows:
+            return None
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for _, _, fl in rows for i, v in enumerate(fl) if v == "Active"})
+        return {"sm_mhz": statistics.median(r[0] for r in rows), "sm_max_mhz": max(r[1] for r in rows),
+                "reasons": reasons, "samples": len(rows)}
+
+
+def kernel_algorithmic(p_info, g, esz_in=4):
+    """Algorithmic bytes (one read of each input, one write of each output) or
+    FP32 flops per launch of every kernel of the hot path."""
+    nproj, H, W = g.nproj, g.det_h, g.det_w
+    Wf, L = p_info["wf"], p_info["planes"]
+    M2, n0, n1, n2 = p_info["m2"], g.n0, g.n1, g.n2
+    c = 8  # complex64
+    return {
+        "filter_rowfft": ("hbm", nproj * H * W * esz_in + nproj * H * Wf * c),
+        "colfft": ("hbm", nproj * H * Wf * c + L * nproj * Wf * c),
+        "grid": ("hbm", L * nproj * Wf * c + L * n0 * M2 * c),
+        "colifft": ("hbm", L * n0 * M2 * c + L * n1 * n0 * c),
+        "zusfft": ("hbm", L * n1 * n0 * c + n0 * n1 * n2 * 4),
+        "filter": ("hbm", nproj * H * W * (esz_in + 4)),
+        # bilinear update: 3 lerps (3 flops each) + accumulate = 10 flops
+        "direct": ("alu", 10 * n0 * n1 * n2 * nproj),
+    }
+
+
+def src_digest() -> str:
+    h = hashlib.sha256()
+    d = os.path.join(ROOT, "paper_2401_11101_gb300", "csrc")
+    for fn in sorted(os.listdir(d)):
+        with open(os.path.join(d, fn), "rb") as f:
+            h.update(fn.encode())
+            h.update(f.read())
+    return h.hexdigest()[:16]
+
+
+def ncu_traffic(workload: str):
+    """Per-launch DRAM bytes from the committed ncu summary, if it was taken on
+    the current kernel sources (else None)."""
+    path = os.path.join(ROOT, "profiles", f"traffic_{workload}.txt")
+    if not os.path.exists(path):
+        return {}
+    out, digest = {}, None
+    for line in open(path):
+        line = line.strip()
+        if line.startswith("# sources"):
+            digest = line.split()[-1]
+        elif line and not line.startswith("#"):
+            parts = line.split()
+            if len(parts) >= 2:
+                out[parts[0]] = float(parts[1])
+    return out if digest == src_digest() else {}
+
+
+# --------------------------------------------------------------------- CPU oracle
+
+def oracle_fourier_sample(d_cpu: np.ndarray, g, ncols: int, seed: int = 7):
+    """The FP64 oracle's Fourier-form FBP on a bounded sample: the filter of
+    every row, the 2D DFT of every projection, the exact type-1 sum on ncols
+    whole columns. Returns (seconds, voxels, threads)."""
+    from oracle import lamino_oracle as O
+    rng = np.random.default_rng(seed)
+    cols = np.stack([rng.integers(0, g.n0, ncols), rng.integers(0, g.n1, ncols)], 1).astype(np.int32)
+    t0 = time.perf_counter()
+    q = O.filter_rows(d_cpu, g, "shepp")
+    O.backproject_fourier_columns(q, g, cols)
+    dt = time.perf_counter() - t0
+    return dt, ncols * g.n2, O.num_threads()
+
+
+# --------------------------------------------------------------------- arms
+
+def run_reference(args, geom, d):
+    """The oracle as it stands on a bounded sample per step (rank 0 only)."""
+    ws, rank, _ = dist_env()
+    if rank != 0:
+        return
+    from oracle import lamino_oracle as O
+    d_cpu = d.cpu().numpy()
+    ncols = 4
+    for _ in range(args.warmup):
+        oracle_fourier_sample(d_cpu, geom, ncols)
+    times, vox = [], 0
+    for _ in range(args.steps):
+        dt, vox, thr = oracle_fourier_sample(d_cpu, geom, ncols)
+        times.append(dt)
+    t = sum(times) / len(times)
+    val = vox / t / 1e9
+    sample = (f"Fourier-form FBP by the FP64 oracle: filter of all {geom.nproj * geom.det_h} rows, "
+              f"2D DFT of all {geom.nproj} projections, exact type-1 sum on {ncols} columns x "
+              f"{geom.n2} slices = {vox} voxels per step")
+    line = {"impl": "reference", "metric": METRIC, "value": val, "unit": "GVox/s",
+            "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": t * 1e3, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": f"{args.workload}: {WORKLOADS[args.workload]}",
+                       "l2": "inputs larger than L2"},
+            "cpu_baseline": {"value": val, "unit": "GVox/s", "cores": thr, "kind": "oracle",
+                             "sample": sample},
+            "e2e": {"value": val, "unit": "GVox/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def run_ours(args, geom, d):
+    from paper_2401_11101_gb300 import lamino as L
+    ws, rank, local = dist_env()
+    dev = torch.device("cuda", local)
+    plan = L.Plan(geom.n0, geom.n1, geom.n2, geom.nproj, geom.det_w, geom.det_h, geom.tilt)
+    info = plan.info
+    vol_f = torch.empty(plan.shape_vol, dtype=torch.float32, device=dev)
+    vol_d = torch.empty(plan.shape_vol, dtype=torch.float32, device=dev)
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)  # > L2 (129 MB)
+    stream = torch.cuda.current_stream(dev)
+
+    def step(ev=None):
+        if ev:
+            ev[0].record(stream)
+        plan.fbp(d, form="fourier", kind="shepp", out=vol_f)
+        if ev:
+            ev[1].record(stream)
+        plan.fbp(d, form="direct", kind="shepp", out=vol_d)
+        if ev:
+            ev[2].record(stream)
+
+    for _ in range(args.warmup):
+        flush.fill_(1.0)
+        step()
+    plan.status()
+    torch.cuda.synchronize(dev)
+
+    gpu_index = int(os.environ.get("CUDA_VISIBLE_DEVICES", str(local)).split(",")[0] or local) \
+        if os.environ.get("CUDA_VISIBLE_DEVICES", "").split(",")[0].isdigit() else local
+    clocks = ClockSampler(gpu_index)
+    evs = [[torch.cuda.Event(enable_timing=True) for _ in range(3)] for _ in range(args.steps)]
+    if ws > 1:
+        torch.distributed.barrier()
+    torch.cuda.synchronize(dev)
+    clocks.start()
+    plan.profile(True)
+    for i in range(args.steps):
+        flush.fill_(1.0)            # L2 flush between timed iterations (outside the events)
+        step(evs[i])
+    torch.cuda.synchronize(dev)
+    recs = plan.profile_read()
+    plan.profile(False)
+    if ws > 1:
+        torch.distributed.barrier()
+    clk = clocks.stop()
+    plan.status()
+
+    t_f = sum(e[0].elapsed_time(e[1]) for e in evs) / args.steps
+    t_d = sum(e[1].elapsed_time(e[2]) for e in evs) / args.steps
+    if ws > 1:
+        tt = torch.tensor([t_f, t_d], device=dev)
+        torch.distributed.all_reduce(tt, op=torch.distributed.ReduceOp.MAX)
+        t_f, t_d = tt.tolist()
+    nvox = geom.nvox
+    value = ws * nvox / (t_f * 1e-3) / 1e9
+    value_d = ws * nvox / (t_d * 1e-3) / 1e9
+
+    # per-kernel live timing and roofline
+    per = {}
+    for name, ms in recs:
+        per.setdefault(name, []).append(ms)
+    peaks, peaks_src = measured_peaks()
+    sm_mhz_max = float(peaks.get("sm_max_mhz", 2070.0))
+    alu_peak = N_SMS * FP32_LANES_PER_SM * 2 * sm_mhz_max * 1e6 / 1e12  # TFLOP/s
+    alg = kernel_algorithmic(info, geom)
+    traffic = ncu_traffic(args.workload)
+    kernels = {}
+    total = sum(sum(v) for v in per.values())
+    for name, v in per.items():
+        avg = sum(v) / len(v)
+        kind, amount = alg.get(name, ("hbm", 0))
+        if kind == "hbm":
+            ach = amount / (avg * 1e-3) / 1e9
+            peak = float(peaks.get("hbm_gbs", 6800.0))
+            unit = "GB/s"
+        else:
+            ach = amount / (avg * 1e-3) / 1e12
+            peak = alu_peak
+            unit = "TFLOP/s"
+        kernels[name] = {"launches": len(v), "avg_ms": round(avg, 4), "share": round(sum(v) / total, 4),
+                         "bound": kind, "achieved": round(ach, 2), "peak": round(peak, 1), "unit": unit,
+                         "frac": round(ach / peak, 4), "algorithmic": amount}
+
+    def roof(name):
+        k = kernels[name]
+        tr = traffic.get(name)
+        return {"kernel": name, "bound": k["bound"], "achieved": k["achieved"], "peak": k["peak"],
+                "unit": k["unit"], "frac": k["frac"], "traffic": tr,
+                "peak_source": f"{peaks_src} ({'hbm_gbs' if k['bound'] == 'hbm' else 'SMs x 128 FP32 lanes x 2 x sm_max_mhz'})"}
+
+    dominant = max(kernels, key=lambda n: kernels[n]["share"])
+    fourier_names = [n for n in kernels if n in ("filter_rowfft", "colfft", "grid", "colifft", "zusfft")]
+    dom_f = max(fourier_names, key=lambda n: kernels[n]["share"])
+
+    # end to end through the C ABI on host buffers (Fourier form)
+    e2e = None
+    if not args.no_e2e:
+        d_host = d.cpu().pin_memory()
+        v_host = torch.empty(plan.shape_vol, dtype=torch.float32).pin_memory()
+        for _ in range(2):
+            plan.fbp_host(d_host, v_host, form="fourier", kind="shepp")
+        ts = []
+        for _ in range(max(3, min(args.steps, 10))):
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            plan.fbp_host(d_host, v_host, form="fourier", kind="shepp")
+            b.record(stream)
+            b.synchronize()
+            ts.append(a.elapsed_time(b))
+        te = sum(ts) / len(ts)
+        if ws > 1:
+            tt = torch.tensor([te], device=dev)
+            torch.distributed.all_reduce(tt, op=torch.distributed.ReduceOp.MAX)
+            te = tt.item()
+        e2e = {"value": ws * nvox / (te * 1e-3) / 1e9, "unit": "GVox/s",
+               "h2d_bytes_per_step": int(d_host.numel() * d_host.element_size()),
+               "d2h_bytes_per_step": int(v_host.numel() * v_host.element_size()),
+               "ms_per_step": te}
+
+    cpu = None
+    if rank == 0 and ws == 1 and not args.no_cpu_baseline:
+        dt, vox, thr = oracle_fourier_sample(d.cpu().numpy(), geom, args.cpu_columns)
+        cpu = {"value": vox / dt / 1e9, "unit": "GVox/s", "cores": thr, "kind": "oracle",
+               "sample": (f"Fourier-form FBP by the FP64 oracle: filter of all "
+                          f"{geom.nproj * geom.det_h} rows, 2D DFT of all {geom.nproj} projections, "
+                          f"exact type-1 sum on {args.cpu_columns} columns x {geom.n2} slices "
+                          f"= {vox} voxels, {dt:.1f} s")}
+
+    if rank == 0:
+        line = {"metric": METRIC, "value": value, "unit": "GVox/s", "n_gpus": ws, "steps": args.steps,
+                "warmup": args.warmup, "ms_per_step": t_f + t_d, "higher_is_better": True,
+                "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+                "config": {"workload": f"{args.workload}: {WORKLOADS[args.workload]}",
+                           "parallelism": f"replicas x{ws} (independent slabs)",
+                           "l2": "inputs larger than L2 and a 256 MB L2 flush between steps",
+                           "usfft": {"R": 2, "w_xy": info["usfft_w"], "w_z": info["usfft_wz"]}},
+                "forms": {"fourier": {"gvox_s": value, "ms": t_f},
+                          "direct": {"gvox_s": value_d, "ms": t_d},
+                          "fourier_over_direct": t_d / t_f},
+                "roofline": roof(dominant), "roofline_fourier": roof(dom_f),
+                "kernels": kernels, "gpu_launches": len(recs),
+                "clocks": clk, "e2e": e2e, "cpu_baseline": cpu}
+        print(json.dumps(line), flush=True)
+    plan.close()
+
+
+def main():
+    args = parse()
+    ws, rank, local = dist_env()
+    if ws > 1:
+        torch.distributed.init_process_group("nccl" if args.impl == "ours" else "gloo")
+    cfg = I.CONFIGS[args.workload]
+    if args.impl == "reference":
+        if rank == 0:
+            dev = "cuda" if torch.cuda.is_available() else "cpu"
+            geom, _, d = I.make_projections(args.workload, device=dev)
+            run_reference(args, geom, d)
+    else:
+        torch.cuda.set_device(local)
+        geom, _, d = I.make_projections(args.workload, device=f"cuda:{local}")
+        d = d.contiguous()
+        run_ours(args, geom, d)
+    if ws > 1:
+        torch.distributed.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

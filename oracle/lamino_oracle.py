@@ -26,7 +26,7 @@ Readings of points the paper leaves open (the same ones the CUDA path uses):
   i.e. trigonometric interpolation of each padded projection at (a.x, b.x).
   The USFFT of the CUDA path is a fast approximation of exactly this sum;
 * padded Fourier detector: Wf >= max(W, 2 u_max + 2), Hf >= max(H, 2 v_max + 2)
-  rounded up to 2^k or 3*2^k, u_max = |(n0, n1)|/2, v_max = u_max sin phi +
+  rounded up to 2^k or 3*2^k, u_max = |(n0, n1)|/2, v_max = u_max |sin phi| +
   n2 cos(phi)/2; the projection sits at offset ((Wf-W)//2, (Hf-H)//2).
 
 Parity of the oracle is pinned by tests/test_oracle_pins.py (closed forms,
@@ -115,7 +115,7 @@ def padded_sizes(geom) -> dict:
     """Filter length Wp and Fourier detector grid Wf x Hf (plan rule above)."""
     W, H = geom.det_w, geom.det_h
     umax = 0.5 * math.hypot(geom.n0, geom.n1)
-    vmax = umax * math.sin(geom.tilt) + 0.5 * geom.n2 * math.cos(geom.tilt)
+    vmax = umax * abs(math.sin(geom.tilt)) + 0.5 * geom.n2 * math.cos(geom.tilt)
     Wp = fft_size(2 * W)
     Wf = fft_size(max(W, 2.0 * umax + 2.0))
     Hf = fft_size(max(H, 2.0 * vmax + 2.0))

@@ -1,0 +1,282 @@
+// Internal declarations of the laminographic FBP library: plan object, error
+// handling and the shared-memory FFT used by every Fourier-side kernel.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <cuda_fp16.h>
+#include <cuda_bf16.h>
+#include <stdint.h>
+
+#include <string>
+#include <vector>
+
+#include "../../include/lamino.h"
+
+namespace lam {
+
+// Largest FFT length any kernel handles (one sequence fits in shared memory).
+constexpr int kMaxFft = 8192;
+
+// Radix schedule of one FFT length: n = product of the stage radices, stage
+// st having radix (rads >> 4 st) & 15; power-of-two radices come first and a
+// radix-3 stage last, so every partial length ns is a power of two. Each stage
+// is done by t = n/e threads holding e complex values in registers.
+struct FftDesc {
+    int n = 0, e = 0, t = 0, nst = 0;
+    unsigned rads = 0;
+    const float2* tw = nullptr;  // device table exp(-2 pi i s/n), s in [0, n)
+};
+
+// Elements per thread: 16 for 2^k lengths (radix-8/4 stages), 12 for 3*2^k
+// lengths (radix-4/2 stages and one radix-3 stage); both fit in registers.
+int fft_elems(int n);
+bool fft_len_ok(int n);
+int fft_size_at_least(double n);   // smallest 2^k or 3*2^k >= n
+
+struct DirectCfg {
+    int tx = 32, ty = 8, tz = 32;    // voxel tile of one CTA (x1, x2, x3)
+    int bw = 0, bh = 0;              // TMA box (detector columns, rows)
+    int stages = 6;                  // TMA pipeline depth
+};
+
+}  // namespace lam
+
+struct lamino_plan_s {
+    int device = 0;
+    int n0 = 0, n1 = 0, n2 = 0, nproj = 0, W = 0, H = 0;
+    double tilt = 0.0;
+    std::vector<double> theta;
+
+    // derived sizes
+    int Wp = 0, Wf = 0, Hf = 0, L = 0, M1 = 0, M2 = 0, M3 = 0;
+    int w = 5, wz = 6, offu = 0, offv = 0;
+    double t1 = 0, t2 = 0, t3 = 0;       // Gaussian widths (grid cells^2) per axis
+    lam::FftDesc fWp, fWf, fHf, fM1, fM2, fM3;
+    int zmax = 0;                        // taps per cell of the x3 gridding table
+
+    // device tables (owned)
+    float2* d_trig = nullptr;      // [nproj] (cos t, sin t) float
+    double* d_trig64 = nullptr;    // [nproj][2] (cos t, sin t) double
+    float* d_filt = nullptr;       // [3][Wp] H(f)/Wp per filter kind, FFT order
+    float2* d_phu = nullptr;       // [Wf] centring phase of column frequency m (signed order)
+    float2* d_phv = nullptr;       // [L]  centring phase of row frequency l
+    float* d_dec1 = nullptr;       // [n0] 1/(M1 psi1(x1))
+    float* d_dec2 = nullptr;       // [n1] 1/(M2 psi2(x2))
+    float* d_dec3 = nullptr;       // [n2] scale/(M3 psi3(x3))
+    int* d_zoff = nullptr;         // [M3+1] CSR offsets of the x3 gridding table
+    int* d_zl = nullptr;           // taps: plane index
+    float* d_zw = nullptr;         // taps: weight (Gaussian x Hermitian factor)
+    float2* d_tw = nullptr;        // all FFT twiddle tables
+    int* d_err = nullptr;          // device error word (bounded waits)
+
+    // workspaces (owned, allocated on first use)
+    void* ws_a = nullptr; size_t ws_a_bytes = 0;   // row spectra R / gridded planes V
+    void* ws_b = nullptr; size_t ws_b_bytes = 0;   // half spectra G / planes P
+    float* q_buf = nullptr; size_t q_buf_bytes = 0; // filtered rows (direct FBP)
+    void* h_in = nullptr; size_t h_in_bytes = 0;   // device copy of host input
+    float* h_vol = nullptr; size_t h_vol_bytes = 0;
+
+    lam::DirectCfg dcfg;
+    bool filter_ok = false;        // Wp is a supported FFT length
+    bool fourier_ok = false;       // Wf, Hf, M1..M3 supported and n even
+    std::string fourier_why;
+
+    // tracing
+    bool profiling = false;
+    std::vector<cudaEvent_t> ev_pool;
+    struct Rec { std::string name; int a, b; };
+    std::vector<Rec> recs;
+    int ev_used = 0;
+
+    std::string err;
+};
+
+namespace lam {
+
+// error helpers -------------------------------------------------------------
+int fail(lamino_plan_t p, int code, const char* fmt, ...);
+int cuda_fail(lamino_plan_t p, cudaError_t e, const char* what);
+void set_global_error(const char* msg);
+
+#define LAM_CUDA(p, call)                                         \
+    do {                                                          \
+        cudaError_t e_ = (call);                                  \
+        if (e_ != cudaSuccess) return lam::cuda_fail((p), e_, #call); \
+    } while (0)
+
+#define LAM_LAUNCH_CHECK(p, what)                                 \
+    do {                                                          \
+        cudaError_t e_ = cudaGetLastError();                      \
+        if (e_ != cudaSuccess) return lam::cuda_fail((p), e_, what); \
+    } while (0)
+
+int ensure_buffer(lamino_plan_t p, void** buf, size_t* have, size_t need, const char* what);
+int set_device(lamino_plan_t p);
+
+// tracing: bracket a launch with events when profiling is on
+void prof_begin(lamino_plan_t p, const char* name, cudaStream_t s);
+void prof_end(lamino_plan_t p, cudaStream_t s);
+struct ProfScope {
+    lamino_plan_t p;
+    cudaStream_t s;
+    ProfScope(lamino_plan_t p_, const char* name, cudaStream_t s_) : p(p_), s(s_) { prof_begin(p, name, s); }
+    ~ProfScope() { prof_end(p, s); }
+};
+
+// kernels' host launchers (defined in the .cu files) ---------------------------
+int launch_filter(lamino_plan_t p, const void* d, int dtype, float* q, int kind,
+                  cudaStream_t s);
+int validate_dtype_kind(lamino_plan_t p, int dtype, int kind);
+int launch_rowfft(lamino_plan_t p, const void* d, int dtype, float2* R, int kind /* -1: no filter */,
+                  cudaStream_t s);
+int run_fourier_after_rows(lamino_plan_t p, float* vol, cudaStream_t s);
+int launch_direct(lamino_plan_t p, const float* q, float* vol, cudaStream_t s);
+int launch_project_direct(lamino_plan_t p, const float* vol, float* d, cudaStream_t s);
+int fourier_workspace(lamino_plan_t p, size_t* a_bytes, size_t* b_bytes);
+
+// device helpers --------------------------------------------------------------
+__device__ __forceinline__ float2 cmul(float2 a, float2 b) {
+    return make_float2(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x);
+}
+__device__ __forceinline__ float2 cadd(float2 a, float2 b) { return make_float2(a.x + b.x, a.y + b.y); }
+__device__ __forceinline__ float2 csub(float2 a, float2 b) { return make_float2(a.x - b.x, a.y - b.y); }
+__device__ __forceinline__ float2 cscale(float2 a, float s) { return make_float2(a.x * s, a.y * s); }
+// multiply by s*i (s = +-1)
+__device__ __forceinline__ float2 cmul_si(float2 a, float s) { return make_float2(-s * a.y, s * a.x); }
+
+template <typename T> __device__ __forceinline__ float load_f(const T* p, size_t i);
+template <> __device__ __forceinline__ float load_f<float>(const float* p, size_t i) { return __ldg(p + i); }
+template <> __device__ __forceinline__ float load_f<__half>(const __half* p, size_t i) { return __half2float(p[i]); }
+template <> __device__ __forceinline__ float load_f<__nv_bfloat16>(const __nv_bfloat16* p, size_t i) {
+    return __bfloat162float(p[i]);
+}
+
+// DFT of length R in registers, exponent sign s (-1 forward, +1 inverse):
+// X_k = sum_r v_r exp(s 2 pi i r k / R).
+template <int R> __device__ __forceinline__ void bfly(float2* v, float s);
+
+template <> __device__ __forceinline__ void bfly<2>(float2* v, float) {
+    float2 a = v[0], b = v[1];
+    v[0] = cadd(a, b);
+    v[1] = csub(a, b);
+}
+template <> __device__ __forceinline__ void bfly<3>(float2* v, float s) {
+    const float h = 0.86602540378443864676f;  // sqrt(3)/2
+    float2 t = cadd(v[1], v[2]);
+    float2 u = cmul_si(csub(v[1], v[2]), s * h);
+    float2 m = make_float2(v[0].x - 0.5f * t.x, v[0].y - 0.5f * t.y);
+    v[0] = cadd(v[0], t);
+    v[1] = cadd(m, u);
+    v[2] = csub(m, u);
+}
+template <> __device__ __forceinline__ void bfly<4>(float2* v, float s) {
+    float2 t0 = cadd(v[0], v[2]), t1 = csub(v[0], v[2]);
+    float2 t2 = cadd(v[1], v[3]), t3 = cmul_si(csub(v[1], v[3]), s);
+    v[0] = cadd(t0, t2);
+    v[2] = csub(t0, t2);
+    v[1] = cadd(t1, t3);
+    v[3] = csub(t1, t3);
+}
+template <> __device__ __forceinline__ void bfly<8>(float2* v, float s) {
+    // split into even / odd halves, two DFT4s, then combine with w8^k
+    float2 e[4] = {v[0], v[2], v[4], v[6]};
+    float2 o[4] = {v[1], v[3], v[5], v[7]};
+    bfly<4>(e, s);
+    bfly<4>(o, s);
+    const float r = 0.70710678118654752440f;
+    // w8^1 = r (1 + s i), w8^2 = s i, w8^3 = r (-1 + s i)
+    float2 o1 = make_float2(r * (o[1].x - s * o[1].y), r * (o[1].y + s * o[1].x));
+    float2 o2 = cmul_si(o[2], s);
+    float2 o3 = make_float2(r * (-o[3].x - s * o[3].y), r * (-o[3].y + s * o[3].x));
+    v[0] = cadd(e[0], o[0]);
+    v[4] = csub(e[0], o[0]);
+    v[1] = cadd(e[1], o1);
+    v[5] = csub(e[1], o1);
+    v[2] = cadd(e[2], o2);
+    v[6] = csub(e[2], o2);
+    v[3] = cadd(e[3], o3);
+    v[7] = csub(e[3], o3);
+}
+
+// One Stockham autosort stage of radix R on a sequence x of length n held in
+// shared memory (the decimation-in-time autosort formulation, see e.g.
+// Govindaraju et al., SC 2008). Each of the t threads of the sequence stages
+// its E/R butterflies' inputs in registers, the block synchronises, and the
+// outputs are written back in place (the barrier separates all reads from all
+// writes). Butterfly j reads x[j + r n/R]; with k = j mod ns it twiddles by
+// exp(-+2 pi i k r/(ns R)), transforms and writes x[(j - k) R + k + r ns].
+template <int E, int R>
+__device__ __forceinline__ void fft_stage(float2* x, const FftDesc& f, int tid, bool active,
+                                          int ns, float s) {
+    static_assert(E % R == 0, "radix must divide the elements per thread");
+    float2 v[E];
+    const int n = f.n, t = f.t, nr = n / R;
+    if (active) {
+#pragma unroll
+        for (int i = 0; i < E / R; ++i) {
+            int j = tid + i * t;
+#pragma unroll
+            for (int r = 0; r < R; ++r) v[i * R + r] = x[j + r * nr];
+        }
+    }
+    __syncthreads();
+    if (active) {
+        const int stride = n / (ns * R);
+#pragma unroll
+        for (int i = 0; i < E / R; ++i) {
+            int j = tid + i * t;
+            int k = j & (ns - 1);  // ns is a power of two
+            if (ns > 1) {
+#pragma unroll
+                for (int r = 1; r < R; ++r) {
+                    // table holds exp(-2 pi i u/n); the inverse uses its conjugate
+                    float2 w = __ldg(f.tw + k * r * stride);
+                    if (s > 0.f) w.y = -w.y;
+                    v[i * R + r] = cmul(v[i * R + r], w);
+                }
+            }
+            bfly<R>(&v[i * R], s);
+            int d = (j - k) * R + k;
+#pragma unroll
+            for (int r = 0; r < R; ++r) x[d + r * ns] = v[i * R + r];
+        }
+    }
+    __syncthreads();
+}
+
+// Complex FFT of the length-f.n sequence at x (shared memory), exponent sign s.
+// Must be called by every thread of the block (it synchronises); threads with
+// active == false only take part in the barriers. Output is in natural order,
+// unnormalised.
+template <int E>
+__device__ __forceinline__ void fft_run(float2* x, const FftDesc& f, int tid, bool active, float s) {
+    active = active && tid < f.t;
+    int ns = 1;
+    for (int st = 0; st < f.nst; ++st) {
+        const int R = (f.rads >> (4 * st)) & 15u;
+        if constexpr (E % 8 == 0) {
+            if (R == 8) fft_stage<E, 8>(x, f, tid, active, ns, s);
+            else fft_stage<E, 4>(x, f, tid, active, ns, s);
+        } else {
+            if (R == 4) fft_stage<E, 4>(x, f, tid, active, ns, s);
+            else if (R == 2) fft_stage<E, 2>(x, f, tid, active, ns, s);
+            else fft_stage<E, 3>(x, f, tid, active, ns, s);
+        }
+        ns *= R;
+    }
+}
+
+// FFTs of nseq sequences at base + i*ld with every thread of the block: groups
+// of blockDim/f.t sequences run side by side (blockDim must be >= f.t).
+template <int E>
+__device__ __forceinline__ void fft_many(float2* base, int ld, int nseq, const FftDesc& f, float s) {
+    const int T = f.t;
+    const int par = blockDim.x / T;
+    const int g = threadIdx.x / T;
+    for (int s0 = 0; s0 < nseq; s0 += par) {
+        const int seq = s0 + g;
+        fft_run<E>(base + (size_t)min(seq, nseq - 1) * ld, f, threadIdx.x % T, g < par && seq < nseq, s);
+    }
+}
+
+}  // namespace lam

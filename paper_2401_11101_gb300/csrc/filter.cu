@@ -1,0 +1,212 @@
+// Row kernels: the filter W of Eq. recon and the detector-row pass of the 2D
+// FFT of the Fourier form (F_2D of Eq. fftadj).
+//
+// Both work on pairs of detector rows packed into one complex sequence
+// z = a + i b. The filter transfer function H(f) is real and even, so
+// IFFT(H . FFT(a + i b)) = (H*a) + i (H*b) with both parts real: one complex
+// FFT pair filters two rows. For the Fourier row pass the two real spectra
+// are separated afterwards with A(m) = (Z(m) + conj Z(-m))/2 and
+// B(m) = (Z(m) - conj Z(-m))/(2i).
+#include <algorithm>
+
+#include "common.cuh"
+
+namespace lam {
+namespace {
+
+// Filter: rows of length W zero-padded to Wp, FFT, x H(f)/Wp, IFFT, crop.
+// One CTA handles `pairs` row pairs; each pair uses t = Wp/E threads.
+template <int E, typename Tin>
+__global__ void __launch_bounds__(512, 1) k_filter(const Tin* __restrict__ d, float* __restrict__ q,
+                                                long nrows, int W, FftDesc fp,
+                                                const float* __restrict__ filt, int pairs) {
+    extern __shared__ float2 sm[];
+    const int T = fp.t, N = fp.n;
+    const int seq = threadIdx.x / T, tid = threadIdx.x % T;
+    const long pair = (long)blockIdx.x * pairs + seq;
+    const long rA = 2 * pair, rB = 2 * pair + 1;
+    const bool active = seq < pairs && rA < nrows;
+    const bool hasB = rB < nrows;
+    float2* x = sm + (size_t)seq * N;
+    if (active) {
+        for (int j = tid; j < N; j += T) {
+            float a = 0.f, b = 0.f;
+            if (j < W) {
+                a = load_f(d, (size_t)rA * W + j);
+                if (hasB) b = load_f(d, (size_t)rB * W + j);
+            }
+            x[j] = make_float2(a, b);
+        }
+    }
+    __syncthreads();
+    fft_run<E>(x, fp, tid, active, -1.f);
+    if (active)
+        for (int j = tid; j < N; j += T) {
+            float h = __ldg(filt + j);
+            x[j] = make_float2(x[j].x * h, x[j].y * h);
+        }
+    __syncthreads();
+    fft_run<E>(x, fp, tid, active, +1.f);
+    if (active)
+        for (int j = tid; j < W; j += T) {
+            float2 v = x[j];
+            q[(size_t)rA * W + j] = v.x;
+            if (hasB) q[(size_t)rB * W + j] = v.y;
+        }
+}
+
+// Fourier row pass. Optionally filters first (EP > 0: FFT of length Wp), then
+// places the W samples at offset offu of a length-Wf row, FFTs it, splits the
+// two real spectra and writes them in signed frequency order mi = m + Wf/2,
+// multiplied by the centring phase exp(2 pi i m cu/Wf) (zero at m = -Wf/2).
+// Output R[row][mi], row = k*H + r.
+template <int EP, int EF, typename Tin>
+__global__ void __launch_bounds__(512, 1) k_rowfft(const Tin* __restrict__ d, float2* __restrict__ R,
+                                                long nrows, int W, int offu, FftDesc fp, FftDesc ff,
+                                                const float* __restrict__ filt,
+                                                const float2* __restrict__ phu, int pairs, int T) {
+    extern __shared__ float2 sm[];
+    const int Np = (EP > 0) ? fp.n : 0, Nf = ff.n;
+    const int seq = threadIdx.x / T, tid = threadIdx.x % T;
+    const long pair = (long)blockIdx.x * pairs + seq;
+    const long rA = 2 * pair, rB = 2 * pair + 1;
+    const bool active = seq < pairs && rA < nrows;
+    const bool hasB = rB < nrows;
+    float2* xp = sm + (size_t)seq * (Np + Nf);
+    float2* xf = xp + Np;
+    if constexpr (EP > 0) {
+        if (active)
+            for (int j = tid; j < Np; j += T) {
+                float a = 0.f, b = 0.f;
+                if (j < W) {
+                    a = load_f(d, (size_t)rA * W + j);
+                    if (hasB) b = load_f(d, (size_t)rB * W + j);
+                }
+                xp[j] = make_float2(a, b);
+            }
+        __syncthreads();
+        fft_run<EP>(xp, fp, tid, active, -1.f);
+        if (active)
+            for (int j = tid; j < Np; j += T) {
+                float h = __ldg(filt + j);
+                xp[j] = make_float2(xp[j].x * h, xp[j].y * h);
+            }
+        __syncthreads();
+        fft_run<EP>(xp, fp, tid, active, +1.f);
+        if (active)
+            for (int j = tid; j < Nf; j += T) {
+                int src = j - offu;
+                xf[j] = (src >= 0 && src < W) ? xp[src] : make_float2(0.f, 0.f);
+            }
+    } else {
+        if (active)
+            for (int j = tid; j < Nf; j += T) {
+                int src = j - offu;
+                float a = 0.f, b = 0.f;
+                if (src >= 0 && src < W) {
+                    a = load_f(d, (size_t)rA * W + src);
+                    if (hasB) b = load_f(d, (size_t)rB * W + src);
+                }
+                xf[j] = make_float2(a, b);
+            }
+    }
+    __syncthreads();
+    fft_run<EF>(xf, ff, tid, active, -1.f);
+    if (active) {
+        const int half = Nf / 2;
+        for (int mi = tid; mi < Nf; mi += T) {
+            int m = mi - half;
+            int i1 = m < 0 ? m + Nf : m;          // index of +m
+            int i2 = m > 0 ? Nf - m : -m;         // index of -m
+            float2 Z = xf[i1], Zc = xf[i2];
+            Zc.y = -Zc.y;
+            float2 A = make_float2(0.5f * (Z.x + Zc.x), 0.5f * (Z.y + Zc.y));
+            float2 Dm = csub(Z, Zc);
+            float2 B = make_float2(0.5f * Dm.y, -0.5f * Dm.x);   // (Z - conj Z(-m)) / (2i)
+            float2 ph = __ldg(phu + mi);
+            R[(size_t)rA * Nf + mi] = cmul(A, ph);
+            if (hasB) R[(size_t)rB * Nf + mi] = cmul(B, ph);
+        }
+    }
+}
+
+int pairs_for(int T, size_t bytes_per_pair) {
+    int pairs = 1;
+    while (pairs * 2 * T <= 512 && (pairs * 2) * bytes_per_pair <= 64 * 1024) pairs *= 2;
+    return pairs;
+}
+
+template <typename Tin>
+int filter_typed(lamino_plan_t p, const Tin* d, float* q, int kind, cudaStream_t s) {
+    const FftDesc& f = p->fWp;
+    long nrows = (long)p->nproj * p->H;
+    long npairs = (nrows + 1) / 2;
+    int pairs = pairs_for(f.t, sizeof(float2) * f.n);
+    size_t smem = sizeof(float2) * f.n * pairs;
+    dim3 grid((unsigned)((npairs + pairs - 1) / pairs));
+    const float* filt = p->d_filt + (size_t)kind * p->Wp;
+    ProfScope prof(p, "filter", s);
+    if (f.e == 16) {
+        cudaFuncSetAttribute(k_filter<16, Tin>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        k_filter<16, Tin><<<grid, pairs * f.t, smem, s>>>(d, q, nrows, p->W, f, filt, pairs);
+    } else {
+        cudaFuncSetAttribute(k_filter<12, Tin>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        k_filter<12, Tin><<<grid, pairs * f.t, smem, s>>>(d, q, nrows, p->W, f, filt, pairs);
+    }
+    LAM_LAUNCH_CHECK(p, "filter kernel");
+    return LAMINO_OK;
+}
+
+template <int EP, int EF, typename Tin>
+int rowfft_launch(lamino_plan_t p, const Tin* d, float2* R, const float* filt, cudaStream_t s) {
+    const int Tp = (EP > 0) ? p->fWp.t : 0;
+    const int T = std::max(Tp, p->fWf.t);
+    const size_t per_pair = sizeof(float2) * ((EP > 0 ? p->Wp : 0) + p->Wf);
+    int pairs = pairs_for(T, per_pair);
+    long nrows = (long)p->nproj * p->H;
+    long npairs = (nrows + 1) / 2;
+    size_t smem = per_pair * pairs;
+    dim3 grid((unsigned)((npairs + pairs - 1) / pairs));
+    auto kern = k_rowfft<EP, EF, Tin>;
+    cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    ProfScope prof(p, EP > 0 ? "filter_rowfft" : "rowfft", s);
+    kern<<<grid, pairs * T, smem, s>>>(d, R, nrows, p->W, p->offu, p->fWp, p->fWf, filt, p->d_phu,
+                                       pairs, T);
+    LAM_LAUNCH_CHECK(p, "row FFT kernel");
+    return LAMINO_OK;
+}
+
+template <typename Tin>
+int rowfft_typed(lamino_plan_t p, const Tin* d, float2* R, int kind, cudaStream_t s) {
+    const float* filt = kind >= 0 ? p->d_filt + (size_t)kind * p->Wp : nullptr;
+    const int ef = p->fWf.e;
+    if (kind < 0) {
+        return ef == 16 ? rowfft_launch<0, 16, Tin>(p, d, R, filt, s)
+                        : rowfft_launch<0, 12, Tin>(p, d, R, filt, s);
+    }
+    const int ep = p->fWp.e;
+    if (ep == 16 && ef == 16) return rowfft_launch<16, 16, Tin>(p, d, R, filt, s);
+    if (ep == 16 && ef == 12) return rowfft_launch<16, 12, Tin>(p, d, R, filt, s);
+    if (ep == 12 && ef == 16) return rowfft_launch<12, 16, Tin>(p, d, R, filt, s);
+    return rowfft_launch<12, 12, Tin>(p, d, R, filt, s);
+}
+
+}  // namespace
+
+int launch_filter(lamino_plan_t p, const void* d, int dtype, float* q, int kind, cudaStream_t s) {
+    switch (dtype) {
+        case LAMINO_F32: return filter_typed(p, (const float*)d, q, kind, s);
+        case LAMINO_F16: return filter_typed(p, (const __half*)d, q, kind, s);
+        default: return filter_typed(p, (const __nv_bfloat16*)d, q, kind, s);
+    }
+}
+
+int launch_rowfft(lamino_plan_t p, const void* d, int dtype, float2* R, int kind, cudaStream_t s) {
+    switch (dtype) {
+        case LAMINO_F32: return rowfft_typed(p, (const float*)d, R, kind, s);
+        case LAMINO_F16: return rowfft_typed(p, (const __half*)d, R, kind, s);
+        default: return rowfft_typed(p, (const __nv_bfloat16*)d, R, kind, s);
+    }
+}
+
+}  // namespace lam

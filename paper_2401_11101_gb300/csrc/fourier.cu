@@ -1,0 +1,367 @@
+// Fourier-form backprojection after the row pass (Eq. fftadj, Sec. 4-5).
+//
+//   colfft  : second pass of the 2D FFT of every projection (along detector
+//             rows v), keeping the k_v >= 0 half of the spectrum and writing
+//             it plane-major: G[l][k][m]. Real projections make the planes
+//             -l the conjugates of planes l (the x3 pass uses 2 Re).
+//   grid    : per k_v plane l and band of T2 rows of the oversampled x2 grid,
+//             Gaussian spreading of every point (k, m) at the frequency of
+//             Eq. uneqspace onto a shared-memory band of the 2x oversampled
+//             plane (the adjoint USFFT's "convolution" step), then the inverse
+//             FFT along x1 of each band row, cropping to n0 and dividing by
+//             M1 psi1(x1). Output V[l][x1][s2] (s2 fastest).
+//   colifft : inverse FFT along x2 of each (l, x1) line, crop to n1, divide
+//             by M2 psi2(x2): P[l][x2][x1]. This completes the 2D USFFT of
+//             the split of Eq. fftfwdsplit.
+//   zusfft  : per column (x1, x2), the 1D USFFT along x3 over the planes
+//             (points xi3 = l cos(phi)/Hf, identical for every column):
+//             gather onto the oversampled x3 grid through a fixed tap table,
+//             inverse FFT, crop, divide by M3 psi3(x3), take the real part.
+#include <math.h>
+
+#include <algorithm>
+
+#include "common.cuh"
+
+namespace lam {
+namespace {
+
+// ---------------------------------------------------------------- colfft
+template <int E>
+__global__ void __launch_bounds__(512, 1) k_colfft(const float2* __restrict__ R, float2* __restrict__ G,
+                                                 int nproj, int H, int Wf, int L, int offv, FftDesc fh,
+                                                 const float2* __restrict__ phv, int C) {
+    extern __shared__ float2 sm[];
+    const int Hf = fh.n, ld = Hf + 1;
+    const int k = blockIdx.y, m0 = blockIdx.x * C;
+    // load C columns of projection k, zero-padded rows, into sequences of length Hf
+    for (int idx = threadIdx.x; idx < C * Hf; idx += blockDim.x) {
+        int c = idx % C, rr = idx / C, r = rr - offv;
+        float2 v = make_float2(0.f, 0.f);
+        if (r >= 0 && r < H) v = R[((size_t)k * H + r) * Wf + m0 + c];
+        sm[c * ld + rr] = v;
+    }
+    __syncthreads();
+    fft_many<E>(sm, ld, C, fh, -1.f);
+    for (int idx = threadIdx.x; idx < C * L; idx += blockDim.x) {
+        int c = idx % C, l = idx / C;
+        G[((size_t)l * nproj + k) * Wf + m0 + c] = cmul(sm[c * ld + l], __ldg(phv + l));
+    }
+}
+
+// ---------------------------------------------------------------- grid
+struct GridArgs {
+    const float2* G;
+    float2* V;
+    const float2* trig;
+    const float* dec1;
+    int nproj, Wf, Hf, n0, M1, M2, T2;
+    float sinphi, c1, c2;  // c = -1/(4t) per axis
+    FftDesc f1;
+};
+
+// Candidate points of one line for one band: the m in [mlo, mhi] with
+// Y(m) = A m + B inside the periodic band [lo + p M2, hi + p M2) for some p,
+// widened by one point on each side (the tap loop decides exactly which rows
+// a point reaches). Returns up to 4 disjoint intervals [ms, me], ascending.
+__device__ __forceinline__ int band_intervals(float A, float B, int mlo, int mhi, float lo, float hi,
+                                              int M2, int* ms, int* me) {
+    if (fabsf(A) < 1e-30f) {
+        float y = B - floorf(B / M2) * M2;  // in [0, M2)
+        bool in = (hi - lo >= (float)M2) || (y >= lo && y < hi) || (y + M2 >= lo && y + M2 < hi) ||
+                  (y - M2 >= lo && y - M2 < hi);
+        if (!in) return 0;
+        ms[0] = mlo;
+        me[0] = mhi;
+        return 1;
+    }
+    float y0 = A * mlo + B, y1 = A * mhi + B;
+    float ymin = fminf(y0, y1), ymax = fmaxf(y0, y1);
+    int p0 = (int)floorf((ymin - hi) / M2), p1 = (int)ceilf((ymax - lo) / M2);
+    int rs[6], re[6], nr = 0;
+    for (int pp = p0; pp <= p1 && nr < 6; ++pp) {
+        float a = lo + (float)pp * M2, b = hi + (float)pp * M2;   // Y in [a, b)
+        float ma = (A > 0) ? (a - B) / A : (b - B) / A;
+        float mb = (A > 0) ? (b - B) / A : (a - B) / A;
+        int s = max(mlo, (int)floorf(ma) - 1);
+        int e = min(mhi, (int)ceilf(mb) + 1);
+        if (s <= e) { rs[nr] = s; re[nr] = e; ++nr; }
+    }
+    // sort by start (A < 0 yields them in descending order) and merge overlaps
+    for (int i = 1; i < nr; ++i)
+        for (int j = i; j > 0 && rs[j] < rs[j - 1]; --j) {
+            int t = rs[j]; rs[j] = rs[j - 1]; rs[j - 1] = t;
+            t = re[j]; re[j] = re[j - 1]; re[j - 1] = t;
+        }
+    int n = 0;
+    for (int i = 0; i < nr; ++i) {
+        if (n > 0 && rs[i] <= me[n - 1] + 1) {
+            me[n - 1] = max(me[n - 1], re[i]);
+        } else if (n < 4) {
+            ms[n] = rs[i];
+            me[n] = re[i];
+            ++n;
+        }
+    }
+    return n;
+}
+
+template <int E, int W>
+__global__ void __launch_bounds__(512, 1) k_grid(GridArgs a) {
+    extern __shared__ float2 sm[];
+    const int M1 = a.M1, M2 = a.M2, T2 = a.T2, ld = M1 + 1;
+    const int band = blockIdx.x, l = blockIdx.y;
+    const int s20 = band * T2;
+    float2* U = sm;  // [T2][M1 + 1]
+    for (int i = threadIdx.x; i < T2 * ld; i += blockDim.x) U[i] = make_float2(0.f, 0.f);
+    __syncthreads();
+
+    const float rho = (float)l * a.sinphi / (float)a.Hf;   // k_v sin(phi)
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
+    const int half = a.Wf / 2;
+    // points whose 2W rows reach the band: Y in [s20 - W, s20 + T2 + W - 1)
+    const float lo = (float)(s20 - W), hi = (float)(s20 + T2 + W - 1);
+    const float2* Gl = a.G + (size_t)l * a.nproj * a.Wf;
+    for (int k = warp; k < a.nproj; k += nwarps) {
+        const float2 cs = __ldg(a.trig + k);
+        // Eq. uneqspace in grid cells: X = M1 (m/Wf cos t + rho sin t),
+        //                               Y = M2 (m/Wf sin t - rho cos t)
+        const float AX = (float)M1 * cs.x / (float)a.Wf, BX = (float)M1 * rho * cs.y;
+        const float AY = (float)M2 * cs.y / (float)a.Wf, BY = -(float)M2 * rho * cs.x;
+        int ms[4], me[4];
+        int ni = band_intervals(AY, BY, -half + 1, half - 1, lo, hi, M2, ms, me);
+        for (int iv = 0; iv < ni; ++iv) {
+            for (int m = ms[iv] + lane; m <= me[iv]; m += 32) {
+                const float2 g = Gl[(size_t)k * a.Wf + (m + half)];
+                float X = fmaf(AX, (float)m, BX);
+                float Y = fmaf(AY, (float)m, BY);
+                X -= floorf(X / M1) * M1;          // X in [0, M1)
+                const float fx = floorf(X), fy = floorf(Y);
+                float gx[2 * W];
+#pragma unroll
+                for (int i = 0; i < 2 * W; ++i) {
+                    float dx = fx - W + 1 + i - X;
+                    gx[i] = __expf(a.c1 * dx * dx);
+                }
+                const int sx0 = (int)fx - W + 1;
+#pragma unroll
+                for (int jy = 0; jy < 2 * W; ++jy) {
+                    int s2 = (int)fy - W + 1 + jy;
+                    int rr = s2 - s20;
+                    rr -= (int)floorf((float)rr / M2) * M2;   // into [0, M2)
+                    if (rr >= T2) continue;
+                    float dy = (float)s2 - Y;
+                    float gy = __expf(a.c2 * dy * dy);
+                    float2 v = make_float2(g.x * gy, g.y * gy);
+                    float2* row = U + rr * ld;
+#pragma unroll
+                    for (int i = 0; i < 2 * W; ++i) {
+                        int s1 = sx0 + i;
+                        s1 += (s1 < 0) ? M1 : 0;
+                        s1 -= (s1 >= M1) ? M1 : 0;
+                        atomicAdd(&row[s1].x, v.x * gx[i]);
+                        atomicAdd(&row[s1].y, v.y * gx[i]);
+                    }
+                }
+            }
+        }
+    }
+    __syncthreads();
+    // inverse FFT of each band row along x1 (sum_s U(s) exp(+2 pi i x s/M1))
+    fft_many<E>(U, ld, T2, a.f1, +1.f);
+    // crop x1 in [-n0/2, n0/2), deconvolve, write V[l][i0][s2] (s2 fastest)
+    const int n0 = a.n0;
+    for (int idx = threadIdx.x; idx < T2 * n0; idx += blockDim.x) {
+        int rr = idx % T2, i0 = idx / T2;
+        int s1 = i0 - n0 / 2;
+        s1 += (s1 < 0) ? M1 : 0;
+        float2 v = cscale(U[rr * ld + s1], __ldg(a.dec1 + i0));
+        a.V[((size_t)l * n0 + i0) * M2 + s20 + rr] = v;
+    }
+}
+
+// ---------------------------------------------------------------- colifft
+template <int E>
+__global__ void __launch_bounds__(512, 1) k_colifft(const float2* __restrict__ V, float2* __restrict__ P,
+                                                  int n0, int n1, FftDesc f2,
+                                                  const float* __restrict__ dec2, int C) {
+    extern __shared__ float2 sm[];
+    const int M2 = f2.n, ld = M2 + 1;
+    const int l = blockIdx.y, i00 = blockIdx.x * C;
+    for (int idx = threadIdx.x; idx < C * M2; idx += blockDim.x) {
+        int c = idx / M2, s = idx % M2;
+        int i0 = i00 + c;
+        sm[c * ld + s] = (i0 < n0) ? V[((size_t)l * n0 + i0) * M2 + s] : make_float2(0.f, 0.f);
+    }
+    __syncthreads();
+    fft_many<E>(sm, ld, C, f2, +1.f);
+    for (int idx = threadIdx.x; idx < C * n1; idx += blockDim.x) {
+        int c = idx % C, i1 = idx / C, i0 = i00 + c;
+        if (i0 >= n0) continue;
+        int s2 = i1 - n1 / 2;
+        s2 += (s2 < 0) ? M2 : 0;
+        P[((size_t)l * n1 + i1) * n0 + i0] = cscale(sm[c * ld + s2], __ldg(dec2 + i1));
+    }
+}
+
+// ---------------------------------------------------------------- zusfft
+template <int E>
+__global__ void __launch_bounds__(512, 1) k_zusfft(const float2* __restrict__ P, float* __restrict__ vol,
+                                                 int L, int n0, int n1, int n2, FftDesc f3,
+                                                 const int* __restrict__ zoff, const int* __restrict__ zl,
+                                                 const float* __restrict__ zw,
+                                                 const float* __restrict__ dec3, int C) {
+    extern __shared__ float2 sm[];
+    const int M3 = f3.n, ld = M3 + 1;
+    const int i1 = blockIdx.y, i00 = blockIdx.x * C;
+    float2* Pl = sm;                   // [L][C]
+    float2* U = sm + (size_t)L * C;    // [C][M3 + 1]
+    for (int idx = threadIdx.x; idx < C * L; idx += blockDim.x) {
+        int c = idx % C, l = idx / C, i0 = i00 + c;
+        Pl[idx] = (i0 < n0) ? P[((size_t)l * n1 + i1) * n0 + i0] : make_float2(0.f, 0.f);
+    }
+    __syncthreads();
+    for (int idx = threadIdx.x; idx < C * M3; idx += blockDim.x) {
+        int c = idx % C, s3 = idx / C;
+        float2 acc = make_float2(0.f, 0.f);
+        const int b = __ldg(zoff + s3), e = __ldg(zoff + s3 + 1);
+        for (int t = b; t < e; ++t) {
+            float wgt = __ldg(zw + t);
+            float2 v = Pl[__ldg(zl + t) * C + c];
+            acc.x = fmaf(wgt, v.x, acc.x);
+            acc.y = fmaf(wgt, v.y, acc.y);
+        }
+        U[c * ld + s3] = acc;
+    }
+    __syncthreads();
+    fft_many<E>(U, ld, C, f3, +1.f);
+    for (int idx = threadIdx.x; idx < C * n2; idx += blockDim.x) {
+        int c = idx % C, i2 = idx / C, i0 = i00 + c;
+        if (i0 >= n0) continue;
+        int s3 = i2 - n2 / 2;
+        s3 += (s3 < 0) ? M3 : 0;
+        vol[((size_t)i2 * n1 + i1) * n0 + i0] = U[c * ld + s3].x * __ldg(dec3 + i2);
+    }
+}
+
+template <typename K>
+void set_smem(K kern, size_t smem) {
+    cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+}
+
+int largest_pow2_divisor_upto(int n, int cap) {
+    int c = 1;
+    while (c * 2 <= cap && n % (c * 2) == 0) c *= 2;
+    return c;
+}
+
+template <int E, int W>
+void launch_grid_kernel(const GridArgs& a, dim3 grid, int threads, size_t smem, cudaStream_t s) {
+    set_smem(k_grid<E, W>, smem);
+    k_grid<E, W><<<grid, threads, smem, s>>>(a);
+}
+
+template <int E>
+int dispatch_grid_w(int w, const GridArgs& a, dim3 grid, int threads, size_t smem, cudaStream_t s) {
+    switch (w) {
+        case 2: launch_grid_kernel<E, 2>(a, grid, threads, smem, s); break;
+        case 3: launch_grid_kernel<E, 3>(a, grid, threads, smem, s); break;
+        case 4: launch_grid_kernel<E, 4>(a, grid, threads, smem, s); break;
+        case 5: launch_grid_kernel<E, 5>(a, grid, threads, smem, s); break;
+        case 6: launch_grid_kernel<E, 6>(a, grid, threads, smem, s); break;
+        case 7: launch_grid_kernel<E, 7>(a, grid, threads, smem, s); break;
+        default: launch_grid_kernel<E, 8>(a, grid, threads, smem, s); break;
+    }
+    return 0;
+}
+
+}  // namespace
+
+int run_fourier_after_rows(lamino_plan_t p, float* vol, cudaStream_t s) {
+    float2* R = (float2*)p->ws_a;   // row spectra   [nproj][H][Wf]
+    float2* G = (float2*)p->ws_b;   // half spectra  [L][nproj][Wf]
+    float2* V = (float2*)p->ws_a;   // x1 pass       [L][n0][M2]   (R is dead by then)
+    float2* P = (float2*)p->ws_b;   // planes        [L][n1][n0]   (G is dead by then)
+
+    // column FFT
+    {
+        const FftDesc& f = p->fHf;
+        int C = largest_pow2_divisor_upto(p->Wf, 16);
+        while (C > 1 && (size_t)C * (f.n + 1) * sizeof(float2) > 100 * 1024) C /= 2;
+        size_t smem = (size_t)C * (f.n + 1) * sizeof(float2);
+        dim3 grid(p->Wf / C, p->nproj);
+        int threads = std::min(512, std::max(C * f.t, 128));
+        ProfScope prof(p, "colfft", s);
+        if (f.e == 16) {
+            set_smem(k_colfft<16>, smem);
+            k_colfft<16><<<grid, threads, smem, s>>>(R, G, p->nproj, p->H, p->Wf, p->L, p->offv, f, p->d_phv, C);
+        } else {
+            set_smem(k_colfft<12>, smem);
+            k_colfft<12><<<grid, threads, smem, s>>>(R, G, p->nproj, p->H, p->Wf, p->L, p->offv, f, p->d_phv, C);
+        }
+        LAM_LAUNCH_CHECK(p, "column FFT kernel");
+    }
+    // gridding + x1 inverse FFT
+    {
+        GridArgs a;
+        a.G = G; a.V = V; a.trig = p->d_trig; a.dec1 = p->d_dec1;
+        a.nproj = p->nproj; a.Wf = p->Wf; a.Hf = p->Hf; a.n0 = p->n0; a.M1 = p->M1; a.M2 = p->M2;
+        a.sinphi = (float)sin(p->tilt);
+        a.c1 = (float)(-1.0 / (4.0 * p->t1));
+        a.c2 = (float)(-1.0 / (4.0 * p->t2));
+        a.f1 = p->fM1;
+        int T2 = 16;
+        while (T2 > 1 && (size_t)T2 * (p->M1 + 1) * sizeof(float2) > 132 * 1024) T2 /= 2;
+        while (p->M2 % T2) T2 /= 2;
+        a.T2 = T2;
+        size_t smem = (size_t)T2 * (p->M1 + 1) * sizeof(float2);
+        int threads = std::min(512, std::max(256, T2 * p->fM1.t));
+        dim3 grid(p->M2 / T2, p->L);
+        ProfScope prof(p, "grid", s);
+        if (p->fM1.e == 16) dispatch_grid_w<16>(p->w, a, grid, threads, smem, s);
+        else dispatch_grid_w<12>(p->w, a, grid, threads, smem, s);
+        LAM_LAUNCH_CHECK(p, "gridding kernel");
+    }
+    // x2 inverse FFT
+    {
+        const FftDesc& f = p->fM2;
+        int C = 16;
+        while (C > 1 && (size_t)C * (f.n + 1) * sizeof(float2) > 132 * 1024) C /= 2;
+        size_t smem = (size_t)C * (f.n + 1) * sizeof(float2);
+        dim3 grid((p->n0 + C - 1) / C, p->L);
+        int threads = std::min(512, std::max(128, C * f.t));
+        ProfScope prof(p, "colifft", s);
+        if (f.e == 16) {
+            set_smem(k_colifft<16>, smem);
+            k_colifft<16><<<grid, threads, smem, s>>>(V, P, p->n0, p->n1, f, p->d_dec2, C);
+        } else {
+            set_smem(k_colifft<12>, smem);
+            k_colifft<12><<<grid, threads, smem, s>>>(V, P, p->n0, p->n1, f, p->d_dec2, C);
+        }
+        LAM_LAUNCH_CHECK(p, "x2 inverse FFT kernel");
+    }
+    // x3 USFFT
+    {
+        const FftDesc& f = p->fM3;
+        int C = 16;
+        auto bytes = [&](int c) { return (size_t)c * ((size_t)p->L + f.n + 1) * sizeof(float2); };
+        while (C > 1 && bytes(C) > 132 * 1024) C /= 2;
+        size_t smem = bytes(C);
+        dim3 grid((p->n0 + C - 1) / C, p->n1);
+        int threads = std::min(512, std::max(128, C * f.t));
+        ProfScope prof(p, "zusfft", s);
+        if (f.e == 16) {
+            set_smem(k_zusfft<16>, smem);
+            k_zusfft<16><<<grid, threads, smem, s>>>(P, vol, p->L, p->n0, p->n1, p->n2, f, p->d_zoff,
+                                                     p->d_zl, p->d_zw, p->d_dec3, C);
+        } else {
+            set_smem(k_zusfft<12>, smem);
+            k_zusfft<12><<<grid, threads, smem, s>>>(P, vol, p->L, p->n0, p->n1, p->n2, f, p->d_zoff,
+                                                     p->d_zl, p->d_zw, p->d_dec3, C);
+        }
+        LAM_LAUNCH_CHECK(p, "x3 USFFT kernel");
+    }
+    return LAMINO_OK;
+}
+
+}  // namespace lam
