@@ -68,10 +68,11 @@ typedef struct lamino_plan_s* lamino_plan_t;
 /* Optional plan parameters; pass NULL for the defaults. Zero fields take the
  * default as well. */
 typedef struct {
-    int usfft_w;     /* Gaussian half-width (grid cells) of the 2D gridding; default 5 */
+    int usfft_w;     /* Gaussian half-width (grid cells) of the 2D gridding; default 4 */
     int usfft_wz;    /* half-width of the 1D gridding along x3; default 6 */
     int wf;          /* override of the padded Fourier detector width Wf */
     int hf;          /* override of the padded Fourier detector height Hf */
+    int grid_rows;   /* rows of the oversampled grid per gridding CTA (power of two; tuning) */
 } lamino_opts;
 
 /* Sizes a plan derived (all integers). */
@@ -90,7 +91,7 @@ typedef struct {
  *   n0,n1,n2 : volume size (x1, x2, x3); each in [1, 8192] (Fourier form:
  *              2*n must round to a length <= 8192).
  *   nproj    : number of projection angles, >= 1.
- *   det_w/h  : detector columns (u) / rows (v); even, <= 16384 / 8192.
+ *   det_w/h  : detector columns (u) / rows (v); >= 1, <= 16384 / 8192.
  *   tilt     : laminographic angle phi in radians, |phi| < pi/2, finite.
  *   angles   : HOST array of nproj rotation angles in radians, or NULL for
  *              theta_k = 2 pi k / nproj. The quadrature weight is pi/nproj

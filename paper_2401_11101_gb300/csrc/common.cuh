@@ -50,6 +50,7 @@ struct lamino_plan_s {
     // derived sizes
     int Wp = 0, Wf = 0, Hf = 0, L = 0, M1 = 0, M2 = 0, M3 = 0;
     int w = 5, wz = 6, offu = 0, offv = 0;
+    int grid_rows = 0;                   // band height of the gridding kernel (0: default)
     double t1 = 0, t2 = 0, t3 = 0;       // Gaussian widths (grid cells^2) per axis
     lam::FftDesc fWp, fWf, fHf, fM1, fM2, fM3;
     int zmax = 0;                        // taps per cell of the x3 gridding table
@@ -198,16 +199,30 @@ template <> __device__ __forceinline__ void bfly<8>(float2* v, float s) {
     v[7] = csub(e[3], o3);
 }
 
-// One Stockham autosort stage of radix R on a sequence x of length n held in
+// Storage views of one FFT sequence in shared memory: interleaved complex
+// (float2) or planar (separate real and imaginary arrays).
+struct SeqC {
+    float2* p;
+    __device__ __forceinline__ float2 ld(int i) const { return p[i]; }
+    __device__ __forceinline__ void st(int i, float2 v) const { p[i] = v; }
+};
+struct SeqP {
+    float* re;
+    float* im;
+    __device__ __forceinline__ float2 ld(int i) const { return make_float2(re[i], im[i]); }
+    __device__ __forceinline__ void st(int i, float2 v) const { re[i] = v.x; im[i] = v.y; }
+};
+
+// One Stockham autosort stage of radix R on a sequence of length n held in
 // shared memory (the decimation-in-time autosort formulation, see e.g.
 // Govindaraju et al., SC 2008). Each of the t threads of the sequence stages
 // its E/R butterflies' inputs in registers, the block synchronises, and the
 // outputs are written back in place (the barrier separates all reads from all
 // writes). Butterfly j reads x[j + r n/R]; with k = j mod ns it twiddles by
 // exp(-+2 pi i k r/(ns R)), transforms and writes x[(j - k) R + k + r ns].
-template <int E, int R>
-__device__ __forceinline__ void fft_stage(float2* x, const FftDesc& f, int tid, bool active,
-                                          int ns, float s) {
+template <int E, int R, typename S>
+__device__ __forceinline__ void fft_stage(S x, const FftDesc& f, int tid, bool active, int ns,
+                                          float s) {
     static_assert(E % R == 0, "radix must divide the elements per thread");
     float2 v[E];
     const int n = f.n, t = f.t, nr = n / R;
@@ -216,7 +231,7 @@ __device__ __forceinline__ void fft_stage(float2* x, const FftDesc& f, int tid, 
         for (int i = 0; i < E / R; ++i) {
             int j = tid + i * t;
 #pragma unroll
-            for (int r = 0; r < R; ++r) v[i * R + r] = x[j + r * nr];
+            for (int r = 0; r < R; ++r) v[i * R + r] = x.ld(j + r * nr);
         }
     }
     __syncthreads();
@@ -238,18 +253,18 @@ __device__ __forceinline__ void fft_stage(float2* x, const FftDesc& f, int tid, 
             bfly<R>(&v[i * R], s);
             int d = (j - k) * R + k;
 #pragma unroll
-            for (int r = 0; r < R; ++r) x[d + r * ns] = v[i * R + r];
+            for (int r = 0; r < R; ++r) x.st(d + r * ns, v[i * R + r]);
         }
     }
     __syncthreads();
 }
 
-// Complex FFT of the length-f.n sequence at x (shared memory), exponent sign s.
+// Complex FFT of the length-f.n sequence x (shared memory), exponent sign s.
 // Must be called by every thread of the block (it synchronises); threads with
 // active == false only take part in the barriers. Output is in natural order,
 // unnormalised.
-template <int E>
-__device__ __forceinline__ void fft_run(float2* x, const FftDesc& f, int tid, bool active, float s) {
+template <int E, typename S>
+__device__ __forceinline__ void fft_run(S x, const FftDesc& f, int tid, bool active, float s) {
     active = active && tid < f.t;
     int ns = 1;
     for (int st = 0; st < f.nst; ++st) {
@@ -266,6 +281,11 @@ __device__ __forceinline__ void fft_run(float2* x, const FftDesc& f, int tid, bo
     }
 }
 
+template <int E>
+__device__ __forceinline__ void fft_run(float2* x, const FftDesc& f, int tid, bool active, float s) {
+    fft_run<E>(SeqC{x}, f, tid, active, s);
+}
+
 // FFTs of nseq sequences at base + i*ld with every thread of the block: groups
 // of blockDim/f.t sequences run side by side (blockDim must be >= f.t).
 template <int E>
@@ -275,7 +295,21 @@ __device__ __forceinline__ void fft_many(float2* base, int ld, int nseq, const F
     const int g = threadIdx.x / T;
     for (int s0 = 0; s0 < nseq; s0 += par) {
         const int seq = s0 + g;
-        fft_run<E>(base + (size_t)min(seq, nseq - 1) * ld, f, threadIdx.x % T, g < par && seq < nseq, s);
+        fft_run<E>(SeqC{base + (size_t)min(seq, nseq - 1) * ld}, f, threadIdx.x % T,
+                   g < par && seq < nseq, s);
+    }
+}
+
+// The same for planar sequences re + i*ld, im + i*ld.
+template <int E>
+__device__ __forceinline__ void fft_many_planar(float* re, float* im, int ld, int nseq,
+                                                const FftDesc& f, float s) {
+    const int T = f.t;
+    const int par = blockDim.x / T;
+    const int g = threadIdx.x / T;
+    for (int s0 = 0; s0 < nseq; s0 += par) {
+        const size_t o = (size_t)min(s0 + g, nseq - 1) * ld;
+        fft_run<E>(SeqP{re + o, im + o}, f, threadIdx.x % T, g < par && s0 + g < nseq, s);
     }
 }
 

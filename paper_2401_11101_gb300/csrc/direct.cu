@@ -94,7 +94,8 @@ __global__ void __launch_bounds__(kThreads) k_direct(const __grid_constant__ CUt
                                                      DirectArgs a) {
     extern __shared__ __align__(128) unsigned char dsm[];
     float* tiles = reinterpret_cast<float*>(dsm);
-    StageMeta* meta = reinterpret_cast<StageMeta*>(dsm + sizeof(float) * (size_t)a.stages * a.stage_floats);
+    StageMeta* meta = reinterpret_cast<StageMeta*>(
+        dsm + sizeof(float) * ((size_t)a.stages * a.stage_floats + (size_t)(TZ + 2) * a.bw));
     uint64_t* full = reinterpret_cast<uint64_t*>(meta + a.stages);
     uint64_t* empty = full + a.stages;
     const int S = a.stages;
@@ -173,18 +174,27 @@ __global__ void __launch_bounds__(kThreads) k_direct(const __grid_constant__ CUt
         const float jf = floorf(jl);
         const float fj = jl - jf;
         const int j0 = min(max((int)jf, 0), bw - 2);
+        // row walk: r(z) = rl + cos(phi) z advances by at most one row per slice
         const float rl = m.rb + m.stsp * (float)tx - m.ctsp * (float)ty;
+        const float rf = floorf(rl);
+        float fr = rl - rf;
+        int r0 = (int)rf;
+        // the walk adds at most TZ rows; the stage buffers carry TZ + 2 rows of
+        // slack after the last stage, so every read stays inside shared memory
+        r0 = min(max(r0, 0), bh - 2);
+        const float* col = tile + j0;
+        const float* p = col + r0 * bw;
+        float h_lo = fmaf(fj, p[1] - p[0], p[0]);              // row r0, lerped in u
+        float h_hi = fmaf(fj, p[bw + 1] - p[bw], p[bw]);       // row r0 + 1
 #pragma unroll
         for (int z = 0; z < TZ; ++z) {
-            const float r = fmaf(cpf, (float)z, rl);
-            const float rf = floorf(r);
-            const float fr = r - rf;
-            const int r0 = min(max((int)rf, 0), bh - 2);
-            const float* p = tile + r0 * bw + j0;
-            const float t0 = p[0], t1 = p[1], b0 = p[bw], b1 = p[bw + 1];
-            const float top = fmaf(fj, t1 - t0, t0);
-            const float bot = fmaf(fj, b1 - b0, b0);
-            acc[z] += fmaf(fr, bot - top, top);
+            acc[z] += fmaf(fr, h_hi - h_lo, h_lo);
+            fr += cpf;
+            const bool adv = fr >= 1.f;
+            fr = adv ? fr - 1.f : fr;
+            p += adv ? bw : 0;
+            h_lo = adv ? h_hi : h_lo;
+            h_hi = fmaf(fj, p[bw + 1] - p[bw], p[bw]);
         }
         __syncwarp();
         if (lane == 0) mbar_arrive(smem_addr(empty + s));
@@ -315,8 +325,8 @@ int launch_direct(lamino_plan_t p, const float* q, float* vol, cudaStream_t s) {
     if (cr != CUDA_SUCCESS) return fail(p, LAMINO_ECUDA, "cuTensorMapEncodeTiled failed (%d)", (int)cr);
     DirectArgs a = make_args(p);
     a.vol = vol;
-    size_t smem = sizeof(float) * (size_t)a.stages * a.stage_floats + sizeof(StageMeta) * a.stages +
-                  2 * sizeof(uint64_t) * a.stages;
+    size_t smem = sizeof(float) * ((size_t)a.stages * a.stage_floats + (size_t)(TZ + 2) * a.bw) +
+                  sizeof(StageMeta) * a.stages + 2 * sizeof(uint64_t) * a.stages;
     dim3 grid((p->n0 + TX - 1) / TX, (p->n1 + TY - 1) / TY, (p->n2 + TZ - 1) / TZ);
     cudaFuncSetAttribute(k_direct, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     ProfScope prof(p, "direct", s);

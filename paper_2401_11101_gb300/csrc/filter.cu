@@ -14,6 +14,28 @@
 namespace lam {
 namespace {
 
+// Rows rA and rA + 1 (if hasB) into x[j] = (a[j - off], b[j - off]) for j in
+// [0, N), zero outside [off, off + W); 8 independent loads in flight per thread.
+template <typename Tin>
+__device__ __forceinline__ void load_pair_rows(const Tin* __restrict__ d, float2* x, long rA, bool hasB,
+                                               int W, int N, int off, int tid, int T) {
+    constexpr int U = 8;
+    const size_t ra = (size_t)rA * W, rb = ra + W;
+    for (int base = tid; base < N; base += U * T) {
+        float a[U], b[U];
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+            const int src = base + u * T - off;
+            const bool in = base + u * T < N && src >= 0 && src < W;
+            a[u] = in ? load_f(d, ra + src) : 0.f;
+            b[u] = (in && hasB) ? load_f(d, rb + src) : 0.f;
+        }
+#pragma unroll
+        for (int u = 0; u < U; ++u)
+            if (base + u * T < N) x[base + u * T] = make_float2(a[u], b[u]);
+    }
+}
+
 // Filter: rows of length W zero-padded to Wp, FFT, x H(f)/Wp, IFFT, crop.
 // One CTA handles `pairs` row pairs; each pair uses t = Wp/E threads.
 template <int E, typename Tin>
@@ -28,16 +50,7 @@ __global__ void __launch_bounds__(512, 1) k_filter(const Tin* __restrict__ d, fl
     const bool active = seq < pairs && rA < nrows;
     const bool hasB = rB < nrows;
     float2* x = sm + (size_t)seq * N;
-    if (active) {
-        for (int j = tid; j < N; j += T) {
-            float a = 0.f, b = 0.f;
-            if (j < W) {
-                a = load_f(d, (size_t)rA * W + j);
-                if (hasB) b = load_f(d, (size_t)rB * W + j);
-            }
-            x[j] = make_float2(a, b);
-        }
-    }
+    if (active) load_pair_rows(d, x, rA, hasB, W, N, 0, tid, T);
     __syncthreads();
     fft_run<E>(x, fp, tid, active, -1.f);
     if (active)
@@ -75,15 +88,7 @@ __global__ void __launch_bounds__(512, 1) k_rowfft(const Tin* __restrict__ d, fl
     float2* xp = sm + (size_t)seq * (Np + Nf);
     float2* xf = xp + Np;
     if constexpr (EP > 0) {
-        if (active)
-            for (int j = tid; j < Np; j += T) {
-                float a = 0.f, b = 0.f;
-                if (j < W) {
-                    a = load_f(d, (size_t)rA * W + j);
-                    if (hasB) b = load_f(d, (size_t)rB * W + j);
-                }
-                xp[j] = make_float2(a, b);
-            }
+        if (active) load_pair_rows(d, xp, rA, hasB, W, Np, 0, tid, T);
         __syncthreads();
         fft_run<EP>(xp, fp, tid, active, -1.f);
         if (active)
@@ -99,16 +104,7 @@ __global__ void __launch_bounds__(512, 1) k_rowfft(const Tin* __restrict__ d, fl
                 xf[j] = (src >= 0 && src < W) ? xp[src] : make_float2(0.f, 0.f);
             }
     } else {
-        if (active)
-            for (int j = tid; j < Nf; j += T) {
-                int src = j - offu;
-                float a = 0.f, b = 0.f;
-                if (src >= 0 && src < W) {
-                    a = load_f(d, (size_t)rA * W + src);
-                    if (hasB) b = load_f(d, (size_t)rB * W + src);
-                }
-                xf[j] = make_float2(a, b);
-            }
+        if (active) load_pair_rows(d, xf, rA, hasB, W, Nf, offu, tid, T);
     }
     __syncthreads();
     fft_run<EF>(xf, ff, tid, active, -1.f);

@@ -28,18 +28,30 @@ namespace {
 
 // ---------------------------------------------------------------- colfft
 template <int E>
-__global__ void __launch_bounds__(512, 1) k_colfft(const float2* __restrict__ R, float2* __restrict__ G,
+__global__ void __launch_bounds__(512, 2) k_colfft(const float2* __restrict__ R, float2* __restrict__ G,
                                                  int nproj, int H, int Wf, int L, int offv, FftDesc fh,
                                                  const float2* __restrict__ phv, int C) {
     extern __shared__ float2 sm[];
     const int Hf = fh.n, ld = Hf + 1;
     const int k = blockIdx.y, m0 = blockIdx.x * C;
     // load C columns of projection k, zero-padded rows, into sequences of length Hf
-    for (int idx = threadIdx.x; idx < C * Hf; idx += blockDim.x) {
-        int c = idx % C, rr = idx / C, r = rr - offv;
-        float2 v = make_float2(0.f, 0.f);
-        if (r >= 0 && r < H) v = R[((size_t)k * H + r) * Wf + m0 + c];
-        sm[c * ld + rr] = v;
+    // (8 independent loads in flight per thread)
+    constexpr int U = 8;
+    const int total = C * Hf;
+    for (int base = threadIdx.x; base < total; base += U * blockDim.x) {
+        float2 v[U];
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+            const int idx = base + u * blockDim.x;
+            const int c = idx % C, r = idx / C - offv;
+            v[u] = (idx < total && r >= 0 && r < H) ? R[((size_t)k * H + r) * Wf + m0 + c]
+                                                    : make_float2(0.f, 0.f);
+        }
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+            const int idx = base + u * blockDim.x;
+            if (idx < total) sm[(idx % C) * ld + idx / C] = v[u];
+        }
     }
     __syncthreads();
     fft_many<E>(sm, ld, C, fh, -1.f);
@@ -66,10 +78,16 @@ struct GridArgs {
 // a point reaches). Returns up to 4 disjoint intervals [ms, me], ascending.
 __device__ __forceinline__ int band_intervals(float A, float B, int mlo, int mhi, float lo, float hi,
                                               int M2, int* ms, int* me) {
-    if (fabsf(A) < 1e-30f) {
-        float y = B - floorf(B / M2) * M2;  // in [0, M2)
-        bool in = (hi - lo >= (float)M2) || (y >= lo && y < hi) || (y + M2 >= lo && y + M2 < hi) ||
-                  (y - M2 >= lo && y - M2 < hi);
+    if (fabsf(A) * (float)(mhi - mlo + 1) < 0.5f) {
+        // the line moves less than half a cell across the band: all or nothing,
+        // tested one cell wider on each side (the tap loop decides exactly)
+        float y = A * 0.5f * (float)(mlo + mhi) + B;
+        y -= floorf(y / M2) * M2;  // in [0, M2]
+        bool in = (hi - lo + 2.f >= (float)M2);
+        for (int pp = -1; pp <= 1 && !in; ++pp) {
+            float yy = y + (float)pp * M2;
+            in = (yy >= lo - 1.f && yy < hi + 1.f);
+        }
         if (!in) return 0;
         ms[0] = mlo;
         me[0] = mhi;
@@ -79,10 +97,13 @@ __device__ __forceinline__ int band_intervals(float A, float B, int mlo, int mhi
     float ymin = fminf(y0, y1), ymax = fmaxf(y0, y1);
     int p0 = (int)floorf((ymin - hi) / M2), p1 = (int)ceilf((ymax - lo) / M2);
     int rs[6], re[6], nr = 0;
+    const float flo = (float)mlo - 2.f, fhi = (float)mhi + 2.f;
     for (int pp = p0; pp <= p1 && nr < 6; ++pp) {
         float a = lo + (float)pp * M2, b = hi + (float)pp * M2;   // Y in [a, b)
         float ma = (A > 0) ? (a - B) / A : (b - B) / A;
         float mb = (A > 0) ? (b - B) / A : (a - B) / A;
+        ma = fminf(fmaxf(ma, flo), fhi);    // keep the int conversion in range
+        mb = fminf(fmaxf(mb, flo), fhi);
         int s = max(mlo, (int)floorf(ma) - 1);
         int e = min(mhi, (int)ceilf(mb) + 1);
         if (s <= e) { rs[nr] = s; re[nr] = e; ++nr; }
@@ -106,92 +127,233 @@ __device__ __forceinline__ int band_intervals(float A, float B, int mlo, int mhi
     return n;
 }
 
+// Exclusive prefix sum of n ints in shared memory (in place), whole block;
+// returns the total. Uses `tmp` (>= 32 ints).
+__device__ __forceinline__ int block_scan(int* v, int n, int* tmp) {
+    const int per = (n + blockDim.x - 1) / blockDim.x;
+    const int b = threadIdx.x * per, e = min(n, b + per);
+    int s = 0;
+    for (int i = b; i < e; ++i) s += v[i];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    int x = s;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        int y = __shfl_up_sync(0xffffffffu, x, o);
+        if (lane >= o) x += y;
+    }
+    if (lane == 31) tmp[warp] = x;
+    __syncthreads();
+    if (warp == 0) {
+        int t = (lane < nw) ? tmp[lane] : 0;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            int y = __shfl_up_sync(0xffffffffu, t, o);
+            if (lane >= o) t += y;
+        }
+        if (lane < nw) tmp[lane] = t;   // inclusive warp totals
+    }
+    __syncthreads();
+    int run = x - s + (warp > 0 ? tmp[warp - 1] : 0);
+    const int total = tmp[nw - 1];
+    for (int i = b; i < e; ++i) {
+        int c = v[i];
+        v[i] = run;
+        run += c;
+    }
+    __syncthreads();
+    return total;
+}
+
+// Gridding of one band of T2 rows of plane l, accumulated in fixed point.
+//
+// Shared-memory float atomics are emulated (about 5x slower than the native
+// int32 shared atomics), so the band accumulates integers: pass 1 bounds the
+// band by S1 = sum of max(|Re v|, |Im v|) and Smax = the largest such value
+// over its points; every tap is scaled by q = min(2^30/S1, 2^21/Smax), so no
+// single contribution reaches 2^22 (the range of the float-to-int rounding
+// below) and no cell sum can reach 2^31 (a cell never holds more than all the
+// band's points). The rounding error is at most 1/2 per tap, about 1e-9 of S1.
+// Taps are rounded to integers with one FMA against 1.5*2^23 (the integer then
+// sits in the low mantissa bits) instead of a float-to-int conversion.
+//
+// The band's points (every line's m-intervals) are numbered through a block
+// prefix sum and dealt to all threads evenly; each thread loops only over the
+// rows of its point that fall inside the band.
+constexpr float kRoundMagic = 12582912.0f;   // 1.5 * 2^23
+constexpr int kRoundMagicBits = 0x4B400000;  // its bit pattern
+
 template <int E, int W>
-__global__ void __launch_bounds__(512, 1) k_grid(GridArgs a) {
-    extern __shared__ float2 sm[];
+__global__ void __launch_bounds__(768, 1) k_grid(GridArgs a) {
+    extern __shared__ float smf[];
     const int M1 = a.M1, M2 = a.M2, T2 = a.T2, ld = M1 + 1;
+    const int nproj = a.nproj;
+    float* Ure = smf;                       // [T2][ld] int32 during accumulation, then float
+    float* Uim = smf + (size_t)T2 * ld;
+    int* iv = reinterpret_cast<int*>(Uim + (size_t)T2 * ld);   // [nproj][8]: 4 x (ms, me)
+    int* off = iv + 8 * nproj;                                   // [nproj + 1] point offsets
+    __shared__ float red_s[32], red_m[32];
+    __shared__ int scan_tmp[32];
     const int band = blockIdx.x, l = blockIdx.y;
     const int s20 = band * T2;
-    float2* U = sm;  // [T2][M1 + 1]
-    for (int i = threadIdx.x; i < T2 * ld; i += blockDim.x) U[i] = make_float2(0.f, 0.f);
-    __syncthreads();
+    int* Ui_re = reinterpret_cast<int*>(Ure);
+    int* Ui_im = reinterpret_cast<int*>(Uim);
+    for (int i = threadIdx.x; i < T2 * ld; i += blockDim.x) { Ui_re[i] = 0; Ui_im[i] = 0; }
 
     const float rho = (float)l * a.sinphi / (float)a.Hf;   // k_v sin(phi)
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
     const int half = a.Wf / 2;
     // points whose 2W rows reach the band: Y in [s20 - W, s20 + T2 + W - 1)
     const float lo = (float)(s20 - W), hi = (float)(s20 + T2 + W - 1);
-    const float2* Gl = a.G + (size_t)l * a.nproj * a.Wf;
-    for (int k = warp; k < a.nproj; k += nwarps) {
+    for (int k = threadIdx.x; k < nproj; k += blockDim.x) {
+        const float2 cs = __ldg(a.trig + k);
+        const float AY = (float)M2 * cs.y / (float)a.Wf, BY = -(float)M2 * rho * cs.x;
+        int ms[4], me[4];
+        const int n = band_intervals(AY, BY, -half + 1, half - 1, lo, hi, M2, ms, me);
+        int* e = iv + 8 * k;
+        int cnt = 0;
+        for (int i = 0; i < 4; ++i) {
+            const bool on = i < n;
+            e[2 * i] = on ? ms[i] : 0;
+            e[2 * i + 1] = on ? me[i] : -1;
+            cnt += on ? me[i] - ms[i] + 1 : 0;
+        }
+        off[k] = cnt;
+    }
+    __syncthreads();
+    const int total = block_scan(off, nproj, scan_tmp);
+    if (threadIdx.x == 0) off[nproj] = total;
+    __syncthreads();
+
+    // point number p -> (line k, m)
+    auto locate = [&](int p, int& k, int& m) {
+        int lo_ = 0, hi_ = nproj;   // off[lo_] <= p < off[hi_]
+        while (hi_ - lo_ > 1) {
+            const int mid = (lo_ + hi_) >> 1;
+            if (off[mid] <= p) lo_ = mid; else hi_ = mid;
+        }
+        k = lo_;
+        int r = p - off[k];
+        const int* e = iv + 8 * k;
+        int i = 0;
+        while (i < 3 && r > e[2 * i + 1] - e[2 * i]) { r -= e[2 * i + 1] - e[2 * i] + 1; ++i; }
+        m = e[2 * i] + r;
+    };
+
+    const float2* Gl = a.G + (size_t)l * nproj * a.Wf;
+    // pass 1: bound the band
+    float lsum = 0.f, lmax = 0.f;
+    for (int p = threadIdx.x; p < total; p += blockDim.x) {
+        int k, m;
+        locate(p, k, m);
+        const float2 g = Gl[(size_t)k * a.Wf + (m + half)];
+        const float v = fmaxf(fabsf(g.x), fabsf(g.y));
+        lsum += v;
+        lmax = fmaxf(lmax, v);
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        lsum += __shfl_xor_sync(0xffffffffu, lsum, o);
+        lmax = fmaxf(lmax, __shfl_xor_sync(0xffffffffu, lmax, o));
+    }
+    if (lane == 0) { red_s[warp] = lsum; red_m[warp] = lmax; }
+    __syncthreads();
+    float S1 = 0.f, Smax = 0.f;
+    for (int i = 0; i < nwarps; ++i) { S1 += red_s[i]; Smax = fmaxf(Smax, red_m[i]); }
+    const float q = (S1 > 0.f) ? fminf(1073741824.0f / S1, 2097152.0f / Smax) : 1.0f;
+
+    // pass 2: spread
+    for (int p = threadIdx.x; p < total; p += blockDim.x) {
+        int k, m;
+        locate(p, k, m);
+        float2 g = Gl[(size_t)k * a.Wf + (m + half)];
+        g.x *= q;
+        g.y *= q;
         const float2 cs = __ldg(a.trig + k);
         // Eq. uneqspace in grid cells: X = M1 (m/Wf cos t + rho sin t),
         //                               Y = M2 (m/Wf sin t - rho cos t)
         const float AX = (float)M1 * cs.x / (float)a.Wf, BX = (float)M1 * rho * cs.y;
         const float AY = (float)M2 * cs.y / (float)a.Wf, BY = -(float)M2 * rho * cs.x;
-        int ms[4], me[4];
-        int ni = band_intervals(AY, BY, -half + 1, half - 1, lo, hi, M2, ms, me);
-        for (int iv = 0; iv < ni; ++iv) {
-            for (int m = ms[iv] + lane; m <= me[iv]; m += 32) {
-                const float2 g = Gl[(size_t)k * a.Wf + (m + half)];
-                float X = fmaf(AX, (float)m, BX);
-                float Y = fmaf(AY, (float)m, BY);
-                X -= floorf(X / M1) * M1;          // X in [0, M1)
-                const float fx = floorf(X), fy = floorf(Y);
-                float gx[2 * W];
+        float X = fmaf(AX, (float)m, BX);
+        const float Y = fmaf(AY, (float)m, BY);
+        X -= floorf(X / M1) * M1;          // X in [0, M1]
+        const float fx = floorf(X), fy = floorf(Y);
+        float gx[2 * W];
+        int col[2 * W];
+        const int sx0 = (int)fx - W + 1;
 #pragma unroll
-                for (int i = 0; i < 2 * W; ++i) {
-                    float dx = fx - W + 1 + i - X;
-                    gx[i] = __expf(a.c1 * dx * dx);
-                }
-                const int sx0 = (int)fx - W + 1;
+        for (int c = 0; c < 2 * W; ++c) {
+            const float dx = fx - W + 1 + c - X;
+            gx[c] = __expf(a.c1 * dx * dx);
+            int s1 = sx0 + c;
+            s1 += (s1 < 0) ? M1 : 0;
+            s1 -= (s1 >= M1) ? M1 : 0;
+            col[c] = s1;
+        }
+        // rows of the point: s2 = fy - W + 1 + jy; band row rr = s2 - s20 (mod M2)
+        int r0 = (int)fy - W + 1 - s20;                 // in (-2 M2 - W, M2)
+        r0 += (r0 < 0) ? M2 : 0;
+        r0 += (r0 < 0) ? M2 : 0;
+        r0 -= (r0 >= M2) ? M2 : 0;                      // now in [0, M2); 2W <= M2
+        for (int jy = 0; jy < 2 * W; ++jy) {
+            int rr = r0 + jy;
+            rr -= (rr >= M2) ? M2 : 0;
+            if ((unsigned)rr >= (unsigned)T2) continue;
+            const float dy = (float)((int)fy - W + 1 + jy) - Y;
+            const float gy = __expf(a.c2 * dy * dy);
+            const float vr = g.x * gy, vi = g.y * gy;
+            int* rre = Ui_re + rr * ld;
+            int* rim = Ui_im + rr * ld;
 #pragma unroll
-                for (int jy = 0; jy < 2 * W; ++jy) {
-                    int s2 = (int)fy - W + 1 + jy;
-                    int rr = s2 - s20;
-                    rr -= (int)floorf((float)rr / M2) * M2;   // into [0, M2)
-                    if (rr >= T2) continue;
-                    float dy = (float)s2 - Y;
-                    float gy = __expf(a.c2 * dy * dy);
-                    float2 v = make_float2(g.x * gy, g.y * gy);
-                    float2* row = U + rr * ld;
-#pragma unroll
-                    for (int i = 0; i < 2 * W; ++i) {
-                        int s1 = sx0 + i;
-                        s1 += (s1 < 0) ? M1 : 0;
-                        s1 -= (s1 >= M1) ? M1 : 0;
-                        atomicAdd(&row[s1].x, v.x * gx[i]);
-                        atomicAdd(&row[s1].y, v.y * gx[i]);
-                    }
-                }
+            for (int c = 0; c < 2 * W; ++c) {
+                atomicAdd(rre + col[c], __float_as_int(fmaf(vr, gx[c], kRoundMagic)) - kRoundMagicBits);
+                atomicAdd(rim + col[c], __float_as_int(fmaf(vi, gx[c], kRoundMagic)) - kRoundMagicBits);
             }
         }
     }
     __syncthreads();
+    // back to float
+    const float inv_q = 1.0f / q;
+    for (int i = threadIdx.x; i < T2 * ld; i += blockDim.x) {
+        Ure[i] = (float)Ui_re[i] * inv_q;
+        Uim[i] = (float)Ui_im[i] * inv_q;
+    }
+    __syncthreads();
     // inverse FFT of each band row along x1 (sum_s U(s) exp(+2 pi i x s/M1))
-    fft_many<E>(U, ld, T2, a.f1, +1.f);
+    fft_many_planar<E>(Ure, Uim, ld, T2, a.f1, +1.f);
     // crop x1 in [-n0/2, n0/2), deconvolve, write V[l][i0][s2] (s2 fastest)
     const int n0 = a.n0;
     for (int idx = threadIdx.x; idx < T2 * n0; idx += blockDim.x) {
         int rr = idx % T2, i0 = idx / T2;
         int s1 = i0 - n0 / 2;
         s1 += (s1 < 0) ? M1 : 0;
-        float2 v = cscale(U[rr * ld + s1], __ldg(a.dec1 + i0));
-        a.V[((size_t)l * n0 + i0) * M2 + s20 + rr] = v;
+        const float dd = __ldg(a.dec1 + i0);
+        a.V[((size_t)l * n0 + i0) * M2 + s20 + rr] = make_float2(Ure[rr * ld + s1] * dd, Uim[rr * ld + s1] * dd);
     }
 }
 
 // ---------------------------------------------------------------- colifft
 template <int E>
-__global__ void __launch_bounds__(512, 1) k_colifft(const float2* __restrict__ V, float2* __restrict__ P,
+__global__ void __launch_bounds__(512, 2) k_colifft(const float2* __restrict__ V, float2* __restrict__ P,
                                                   int n0, int n1, FftDesc f2,
                                                   const float* __restrict__ dec2, int C) {
     extern __shared__ float2 sm[];
     const int M2 = f2.n, ld = M2 + 1;
     const int l = blockIdx.y, i00 = blockIdx.x * C;
-    for (int idx = threadIdx.x; idx < C * M2; idx += blockDim.x) {
-        int c = idx / M2, s = idx % M2;
-        int i0 = i00 + c;
-        sm[c * ld + s] = (i0 < n0) ? V[((size_t)l * n0 + i0) * M2 + s] : make_float2(0.f, 0.f);
+    constexpr int U = 8;
+    const int total = C * M2;
+    for (int base = threadIdx.x; base < total; base += U * blockDim.x) {
+        float2 v[U];
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+            const int idx = base + u * blockDim.x;
+            const int i0 = i00 + idx / M2;
+            v[u] = (idx < total && i0 < n0) ? V[((size_t)l * n0 + i0) * M2 + idx % M2] : make_float2(0.f, 0.f);
+        }
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+            const int idx = base + u * blockDim.x;
+            if (idx < total) sm[(idx / M2) * ld + idx % M2] = v[u];
+        }
     }
     __syncthreads();
     fft_many<E>(sm, ld, C, f2, +1.f);
@@ -206,7 +368,7 @@ __global__ void __launch_bounds__(512, 1) k_colifft(const float2* __restrict__ V
 
 // ---------------------------------------------------------------- zusfft
 template <int E>
-__global__ void __launch_bounds__(512, 1) k_zusfft(const float2* __restrict__ P, float* __restrict__ vol,
+__global__ void __launch_bounds__(512, 2) k_zusfft(const float2* __restrict__ P, float* __restrict__ vol,
                                                  int L, int n0, int n1, int n2, FftDesc f3,
                                                  const int* __restrict__ zoff, const int* __restrict__ zl,
                                                  const float* __restrict__ zw,
@@ -216,9 +378,21 @@ __global__ void __launch_bounds__(512, 1) k_zusfft(const float2* __restrict__ P,
     const int i1 = blockIdx.y, i00 = blockIdx.x * C;
     float2* Pl = sm;                   // [L][C]
     float2* U = sm + (size_t)L * C;    // [C][M3 + 1]
-    for (int idx = threadIdx.x; idx < C * L; idx += blockDim.x) {
-        int c = idx % C, l = idx / C, i0 = i00 + c;
-        Pl[idx] = (i0 < n0) ? P[((size_t)l * n1 + i1) * n0 + i0] : make_float2(0.f, 0.f);
+    constexpr int NB = 8;
+    const int total = C * L;
+    for (int base = threadIdx.x; base < total; base += NB * blockDim.x) {
+        float2 v[NB];
+#pragma unroll
+        for (int u = 0; u < NB; ++u) {
+            const int idx = base + u * blockDim.x;
+            const int i0 = i00 + idx % C;
+            v[u] = (idx < total && i0 < n0) ? P[((size_t)(idx / C) * n1 + i1) * n0 + i0] : make_float2(0.f, 0.f);
+        }
+#pragma unroll
+        for (int u = 0; u < NB; ++u) {
+            const int idx = base + u * blockDim.x;
+            if (idx < total) Pl[idx] = v[u];
+        }
     }
     __syncthreads();
     for (int idx = threadIdx.x; idx < C * M3; idx += blockDim.x) {
@@ -310,12 +484,15 @@ int run_fourier_after_rows(lamino_plan_t p, float* vol, cudaStream_t s) {
         a.c1 = (float)(-1.0 / (4.0 * p->t1));
         a.c2 = (float)(-1.0 / (4.0 * p->t2));
         a.f1 = p->fM1;
-        int T2 = 16;
+        int T2 = p->grid_rows > 0 ? p->grid_rows : 16;
         while (T2 > 1 && (size_t)T2 * (p->M1 + 1) * sizeof(float2) > 132 * 1024) T2 /= 2;
         while (p->M2 % T2) T2 /= 2;
         a.T2 = T2;
-        size_t smem = (size_t)T2 * (p->M1 + 1) * sizeof(float2);
-        int threads = std::min(512, std::max(256, T2 * p->fM1.t));
+        // band accumulator (planar) + per-line intervals and point offsets
+        size_t smem = (size_t)T2 * (p->M1 + 1) * sizeof(float2) + sizeof(int) * (9 * (size_t)p->nproj + 1);
+        if (smem > 220 * 1024)
+            return fail(p, LAMINO_EUNSUPPORTED, "gridding tile of %zu bytes exceeds shared memory", smem);
+        int threads = 768;
         dim3 grid(p->M2 / T2, p->L);
         ProfScope prof(p, "grid", s);
         if (p->fM1.e == 16) dispatch_grid_w<16>(p->w, a, grid, threads, smem, s);

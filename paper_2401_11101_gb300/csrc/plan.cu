@@ -326,6 +326,8 @@ void direct_config(lamino_plan_t p) {
     double diag = sqrt((double)(c.tx - 1) * (c.tx - 1) + (double)(c.ty - 1) * (c.ty - 1));
     int need_w = (int)floor(diag) + 1 /*guard*/ + 2 /*floor+neighbour*/ + 3 /*align*/ + 1;
     c.bw = (need_w + 3) / 4 * 4;
+    // row pitch = 12 or 20 mod 32 words: rows 1..7 apart fall in different banks
+    while (c.bw % 32 != 12 && c.bw % 32 != 20) c.bw += 4;
     double span_r = fabs(sin(p->tilt)) * diag + cos(p->tilt) * (c.tz - 1);
     c.bh = (int)floor(span_r) + 1 /*guard*/ + 2 /*floor+neighbour*/ + 2;
 }
@@ -364,8 +366,8 @@ int lamino_plan(lamino_plan_t* out, int n0, int n1, int n2, int nproj, int det_w
         return fail(nullptr, LAMINO_EINVAL, "volume size %dx%dx%d out of range [1, 8192]", n0, n1, n2);
     if (nproj < 1 || nproj > (1 << 20))
         return fail(nullptr, LAMINO_EINVAL, "nproj %d out of range", nproj);
-    if (det_w < 2 || det_h < 2 || det_w > 16384 || det_h > 8192 || (det_w & 1) || (det_h & 1))
-        return fail(nullptr, LAMINO_EINVAL, "detector %dx%d must be even, <= 16384x8192", det_w, det_h);
+    if (det_w < 1 || det_h < 1 || det_w > 16384 || det_h > 8192)
+        return fail(nullptr, LAMINO_EINVAL, "detector %dx%d out of range [1, 16384]x[1, 8192]", det_w, det_h);
     if (!isfinite(tilt) || fabs(tilt) >= kPi / 2)
         return fail(nullptr, LAMINO_EINVAL, "tilt %g rad must be finite with |tilt| < pi/2", tilt);
     if (angles)
@@ -396,16 +398,21 @@ int lamino_plan(lamino_plan_t* out, int n0, int n1, int n2, int nproj, int det_w
     p->Hf = fft_size_at_least(std::max((double)det_h, 2.0 * vmax + 2.0));
     if (opts && opts->wf) p->Wf = opts->wf;
     if (opts && opts->hf) p->Hf = opts->hf;
-    p->w = (opts && opts->usfft_w) ? opts->usfft_w : 5;
+    p->w = (opts && opts->usfft_w) ? opts->usfft_w : 4;
     p->wz = (opts && opts->usfft_wz) ? opts->usfft_wz : 6;
+    p->grid_rows = (opts && opts->grid_rows > 0) ? opts->grid_rows : 0;
+    if (p->grid_rows & (p->grid_rows - 1)) {
+        free_plan(p);
+        return fail(nullptr, LAMINO_EINVAL, "grid_rows must be a power of two");
+    }
     if (p->w < 2 || p->w > 8 || p->wz < 2 || p->wz > 8) {
         free_plan(p);
         return fail(nullptr, LAMINO_EINVAL, "usfft half-widths must be in [2, 8]");
     }
-    if (p->Wf < det_w || p->Hf < det_h || ((p->Wf - det_w) & 1) || ((p->Hf - det_h) & 1)) {
+    if (p->Wf < det_w || p->Hf < det_h) {
         free_plan(p);
-        return fail(nullptr, LAMINO_EINVAL, "Fourier grid %dx%d must cover the detector with even margins",
-                    p->Wf, p->Hf);
+        return fail(nullptr, LAMINO_EINVAL, "Fourier grid %dx%d must cover the %dx%d detector",
+                    p->Wf, p->Hf, det_w, det_h);
     }
     p->L = p->Hf / 2;
     p->offu = (p->Wf - det_w) / 2;

@@ -42,7 +42,7 @@ class LaminoError(RuntimeError):
 
 class _Opts(ctypes.Structure):
     _fields_ = [("usfft_w", ctypes.c_int), ("usfft_wz", ctypes.c_int),
-                ("wf", ctypes.c_int), ("hf", ctypes.c_int)]
+                ("wf", ctypes.c_int), ("hf", ctypes.c_int), ("grid_rows", ctypes.c_int)]
 
 
 class _KTime(ctypes.Structure):
@@ -99,12 +99,12 @@ class Plan:
     """A reconstruction plan for one geometry (owns device tables/workspaces)."""
 
     def __init__(self, n0, n1, n2, nproj, det_w, det_h, tilt, angles=None, usfft_w=0,
-                 usfft_wz=0, wf=0, hf=0, device=None):
+                 usfft_wz=0, wf=0, hf=0, grid_rows=0, device=None):
         self._lib = load_library()
         self.device = torch.device("cuda", torch.cuda.current_device() if device is None
                                    else torch.device(device).index or 0)
         self._h = ctypes.c_void_p()
-        opts = _Opts(usfft_w, usfft_wz, wf, hf)
+        opts = _Opts(usfft_w, usfft_wz, wf, hf, grid_rows)
         ang = None
         if angles is not None:
             arr = (ctypes.c_double * nproj)(*[float(a) for a in angles])

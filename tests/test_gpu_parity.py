@@ -68,8 +68,8 @@ def test_filter_parity(L, kind, dtype):
 
 
 def test_filter_ragged_rows(L):
-    # odd number of rows (unpaired last row) and a width that is not a multiple of 4
-    g = I.Geometry(8, 8, 8, 3, 5, 22, 0.3)
+    # odd number of rows (unpaired last row), odd width not a multiple of 4
+    g = I.Geometry(8, 8, 8, 3, 5, 21, 0.3)
     d = torch.as_tensor(I.random_projections(g, 21), dtype=torch.float32)
     with plan_for(L, g) as p:
         q = p.filter(d.cuda(), "ramp").cpu().numpy()
@@ -98,6 +98,7 @@ def test_direct_parity_c1(L):
     I.Geometry(32, 40, 35, 7, 40, 62, math.radians(-25.0)),    # negative tilt, odd n2
     I.Geometry(8, 8, 8, 1, 8, 12, math.radians(20.0)),         # one angle, tiny
     I.Geometry(24, 24, 16, 16, 18, 42, math.radians(60.0)),    # steep tilt, detector truncation
+    I.Geometry(20, 20, 10, 10, 13, 27, math.radians(20.0)),    # odd detector sizes (unaligned rows)
 ])
 def test_direct_parity_edge_cases(L, geom):
     q = I.random_projections(geom, 22).astype(np.float32)
@@ -169,6 +170,7 @@ def test_fourier_parity_c1(L):
     I.Geometry(16, 16, 8, 12, 10, 26, 0.0),                    # tomography limit
     I.Geometry(32, 32, 16, 7, 24, 46, math.radians(-20.0)),   # negative tilt, odd nproj
     I.Geometry(16, 16, 16, 1, 16, 24, math.radians(40.0)),    # one angle
+    I.Geometry(16, 24, 8, 9, 11, 23, math.radians(25.0)),     # odd detector sizes
 ])
 def test_fourier_parity_edge_cases(L, geom):
     q = I.random_projections(geom, 26).astype(np.float32)
@@ -177,6 +179,18 @@ def test_fourier_parity_edge_cases(L, geom):
     ref = O.backproject_fourier(q, geom)
     e = rel(v, ref)
     print(f"fourier {geom} relL2 = {e:.2e}")
+    assert e <= 1e-4
+
+
+@pytest.mark.parametrize("w,wz", [(4, 6), (5, 6), (6, 6), (4, 4)])
+def test_fourier_kernel_width_c1(L, w, wz):
+    # the USFFT error shrinks with the Gaussian half-width (R = 2)
+    g, d = c1_inputs()
+    q = O.filter_rows(d.numpy(), g, "shepp").astype(np.float32)
+    with plan_for(L, g, usfft_w=w, usfft_wz=wz) as p:
+        v = p.backproject_fourier(torch.as_tensor(q).cuda()).cpu().numpy()
+    e = rel(v, O.backproject_fourier(q, g))
+    print(f"fourier c1 w={w} wz={wz} relL2 = {e:.2e}")
     assert e <= 1e-4
 
 
@@ -246,10 +260,13 @@ def test_c2_full_size_sampled_parity(L, c2_case):
 def test_fbp_host_matches_device(L):
     g, d = c1_inputs()
     with plan_for(L, g) as p:
-        dev = p.fbp(d.cuda(), form="fourier", kind="shepp").cpu()
         out = torch.empty(p.shape_vol, dtype=torch.float32).pin_memory()
+        dev = p.fbp(d.cuda(), form="direct", kind="shepp").cpu()
+        p.fbp_host(d.pin_memory(), out, form="direct", kind="shepp")
+        assert torch.equal(dev, out)          # deterministic form: bit-exact
+        dev = p.fbp(d.cuda(), form="fourier", kind="shepp").cpu()
         p.fbp_host(d.pin_memory(), out, form="fourier", kind="shepp")
-    assert torch.equal(dev, out)
+        assert rel(out.numpy(), dev.numpy()) < 1e-6
 
 
 def test_repeat_calls_are_deterministic(L):
