@@ -67,7 +67,7 @@ struct GridArgs {
     float2* V;
     const float2* trig;
     const float* dec1;
-    int nproj, Wf, Hf, n0, M1, M2, T2;
+    int nproj, Wf, Hf, n0, M1, M2, T2, ld;   // ld: row pitch of the band accumulator
     float sinphi, c1, c2;  // c = -1/(4t) per axis
     FftDesc f1;
 };
@@ -185,12 +185,15 @@ constexpr int kRoundMagicBits = 0x4B400000;  // its bit pattern
 template <int E, int W>
 __global__ void __launch_bounds__(768, 1) k_grid(GridArgs a) {
     extern __shared__ float smf[];
-    const int M1 = a.M1, M2 = a.M2, T2 = a.T2, ld = M1 + 1;
+    const int M1 = a.M1, M2 = a.M2, T2 = a.T2, ld = a.ld;
     const int nproj = a.nproj;
     float* Ure = smf;                       // [T2][ld] int32 during accumulation, then float
     float* Uim = smf + (size_t)T2 * ld;
-    int* iv = reinterpret_cast<int*>(Uim + (size_t)T2 * ld);   // [nproj][8]: 4 x (ms, me)
-    int* off = iv + 8 * nproj;                                   // [nproj + 1] point offsets
+    // compact list of the band's non-empty m-intervals: ioff[i] = first point
+    // number, ikm[i] = (line << 13) | (m start + 4096); ioff[n] = total
+    int* ioff = reinterpret_cast<int*>(Uim + (size_t)T2 * ld);
+    int* ikm = ioff + 4 * nproj + 1;
+    int* lcnt = ikm + 4 * nproj;            // [nproj] per-line interval counts (scan)
     __shared__ float red_s[32], red_m[32];
     __shared__ int scan_tmp[32];
     const int band = blockIdx.x, l = blockIdx.y;
@@ -204,47 +207,66 @@ __global__ void __launch_bounds__(768, 1) k_grid(GridArgs a) {
     const int half = a.Wf / 2;
     // points whose 2W rows reach the band: Y in [s20 - W, s20 + T2 + W - 1)
     const float lo = (float)(s20 - W), hi = (float)(s20 + T2 + W - 1);
-    for (int k = threadIdx.x; k < nproj; k += blockDim.x) {
-        const float2 cs = __ldg(a.trig + k);
-        const float AY = (float)M2 * cs.y / (float)a.Wf, BY = -(float)M2 * rho * cs.x;
-        int ms[4], me[4];
-        const int n = band_intervals(AY, BY, -half + 1, half - 1, lo, hi, M2, ms, me);
-        int* e = iv + 8 * k;
-        int cnt = 0;
-        for (int i = 0; i < 4; ++i) {
-            const bool on = i < n;
-            e[2 * i] = on ? ms[i] : 0;
-            e[2 * i + 1] = on ? me[i] : -1;
-            cnt += on ? me[i] - ms[i] + 1 : 0;
+    // one thread per line: its intervals stay in registers across the scans
+    const int per = (nproj + blockDim.x - 1) / blockDim.x;   // lines per thread (<= 4)
+    int ms[4][4], me[4][4], nint[4];
+#pragma unroll
+    for (int t = 0; t < 4; ++t) {
+        nint[t] = 0;
+        const int k = threadIdx.x * per + t;
+        if (t < per && k < nproj) {
+            const float2 cs = __ldg(a.trig + k);
+            const float AY = (float)M2 * cs.y / (float)a.Wf, BY = -(float)M2 * rho * cs.x;
+            nint[t] = band_intervals(AY, BY, -half + 1, half - 1, lo, hi, M2, ms[t], me[t]);
+            lcnt[k] = nint[t];
         }
-        off[k] = cnt;
     }
     __syncthreads();
-    const int total = block_scan(off, nproj, scan_tmp);
-    if (threadIdx.x == 0) off[nproj] = total;
+    const int nintv = block_scan(lcnt, nproj, scan_tmp);
+#pragma unroll
+    for (int t = 0; t < 4; ++t) {
+        const int k = threadIdx.x * per + t;
+        if (t < per && k < nproj) {
+            int o = lcnt[k];
+            for (int i = 0; i < nint[t]; ++i) {
+                ioff[o + i] = me[t][i] - ms[t][i] + 1;
+                ikm[o + i] = (k << 13) | (ms[t][i] + 4096);
+            }
+        }
+    }
+    __syncthreads();
+    const int total = block_scan(ioff, nintv, scan_tmp);
+    if (threadIdx.x == 0) ioff[nintv] = total;
     __syncthreads();
 
-    // point number p -> (line k, m)
-    auto locate = [&](int p, int& k, int& m) {
-        int lo_ = 0, hi_ = nproj;   // off[lo_] <= p < off[hi_]
-        while (hi_ - lo_ > 1) {
-            const int mid = (lo_ + hi_) >> 1;
-            if (off[mid] <= p) lo_ = mid; else hi_ = mid;
+    // A warp takes 32 consecutive point numbers: lane 0 finds the interval of
+    // the first one, every lane then steps forward from it.
+    auto locate = [&](int base, int& k, int& m) -> bool {
+        int iv = 0;
+        if (lane == 0) {
+            int a0 = 0, b0 = nintv;   // ioff[a0] <= base < ioff[b0]
+            while (b0 - a0 > 1) {
+                const int mid = (a0 + b0) >> 1;
+                if (ioff[mid] <= base) a0 = mid; else b0 = mid;
+            }
+            iv = a0;
         }
-        k = lo_;
-        int r = p - off[k];
-        const int* e = iv + 8 * k;
-        int i = 0;
-        while (i < 3 && r > e[2 * i + 1] - e[2 * i]) { r -= e[2 * i + 1] - e[2 * i] + 1; ++i; }
-        m = e[2 * i] + r;
+        iv = __shfl_sync(0xffffffffu, iv, 0);
+        const int p = base + lane;
+        if (p >= total) return false;
+        while (ioff[iv + 1] <= p) ++iv;
+        const int km = ikm[iv];
+        k = km >> 13;
+        m = (km & 8191) - 4096 + (p - ioff[iv]);
+        return true;
     };
 
     const float2* Gl = a.G + (size_t)l * nproj * a.Wf;
     // pass 1: bound the band
     float lsum = 0.f, lmax = 0.f;
-    for (int p = threadIdx.x; p < total; p += blockDim.x) {
+    for (int base = warp * 32; base < total; base += nwarps * 32) {
         int k, m;
-        locate(p, k, m);
+        if (!locate(base, k, m)) continue;
         const float2 g = Gl[(size_t)k * a.Wf + (m + half)];
         const float v = fmaxf(fabsf(g.x), fabsf(g.y));
         lsum += v;
@@ -262,9 +284,9 @@ __global__ void __launch_bounds__(768, 1) k_grid(GridArgs a) {
     const float q = (S1 > 0.f) ? fminf(1073741824.0f / S1, 2097152.0f / Smax) : 1.0f;
 
     // pass 2: spread
-    for (int p = threadIdx.x; p < total; p += blockDim.x) {
+    for (int base = warp * 32; base < total; base += nwarps * 32) {
         int k, m;
-        locate(p, k, m);
+        if (!locate(base, k, m)) continue;
         float2 g = Gl[(size_t)k * a.Wf + (m + half)];
         g.x *= q;
         g.y *= q;
@@ -484,12 +506,19 @@ int run_fourier_after_rows(lamino_plan_t p, float* vol, cudaStream_t s) {
         a.c1 = (float)(-1.0 / (4.0 * p->t1));
         a.c2 = (float)(-1.0 / (4.0 * p->t2));
         a.f1 = p->fM1;
+        // Row pitch = 5 (mod 32) words: lanes holding consecutive points of one
+        // line (steps of ~1.33 cells) then fall in different banks for all but
+        // a narrow wedge of line directions (a pitch of 1 mod 32 stacks every
+        // near-anti-diagonal line into one bank).
+        a.ld = p->M1 + ((5 - p->M1) % 32 + 32) % 32;
         int T2 = p->grid_rows > 0 ? p->grid_rows : 16;
-        while (T2 > 1 && (size_t)T2 * (p->M1 + 1) * sizeof(float2) > 132 * 1024) T2 /= 2;
+        while (T2 > 1 && (size_t)T2 * a.ld * sizeof(float2) > 132 * 1024) T2 /= 2;
         while (p->M2 % T2) T2 /= 2;
         a.T2 = T2;
-        // band accumulator (planar) + per-line intervals and point offsets
-        size_t smem = (size_t)T2 * (p->M1 + 1) * sizeof(float2) + sizeof(int) * (9 * (size_t)p->nproj + 1);
+        // band accumulator (planar) + compact interval list + per-line counts
+        if (p->nproj > 4 * 768 || p->Wf > 8192)
+            return fail(p, LAMINO_EUNSUPPORTED, "gridding supports up to 3072 angles and Wf <= 8192");
+        size_t smem = (size_t)T2 * a.ld * sizeof(float2) + sizeof(int) * (9 * (size_t)p->nproj + 1);
         if (smem > 220 * 1024)
             return fail(p, LAMINO_EUNSUPPORTED, "gridding tile of %zu bytes exceeds shared memory", smem);
         int threads = 768;
