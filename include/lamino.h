@@ -150,6 +150,34 @@ int lamino_backproject_fourier(lamino_plan_t plan, const void* q, int dtype, flo
                                cudaStream_t stream);
 
 /*
+ * lamino_backproject_fourier_noalloc -- the same result as
+ * lamino_backproject_fourier, computed without allocating any device memory.
+ * The paper has no counterpart to this call; it exists for callers that must
+ * not allocate at reconstruction time: a streaming loop that may not stall on
+ * the device allocator between frames, a process whose device memory is owned
+ * by a pool or allocator that forbids stray cudaMalloc calls, or code that
+ * records its work into a CUDA graph, where allocating inside the recorded
+ * region is not permitted.
+ *   - Its workspace is one static device array of 64 MiB held by every GPU that
+ *     loads this library, until the process exits. Geometries whose Fourier
+ *     workspace (lamino_workspace_bytes with LAMINO_FOURIER) exceeds it are
+ *     rejected with LAMINO_EINVAL and a message giving both sizes; use
+ *     lamino_backproject_fourier for those.
+ *   - The plan itself (lamino_plan) still allocates its tables: create it while
+ *     allocation is allowed. This call allocates nothing and calls no
+ *     cudaMalloc/cudaFree; tracing (lamino_profile) is off during it.
+ *   - The first call on each device looks up the array's device address with
+ *     cudaGetSymbolAddress; make that first call before any stream capture.
+ *   - Every call, from every plan and stream, shares the one array, and the
+ *     array keeps the previous call's contents (nothing in it needs to start at
+ *     zero). Calls whose execution overlaps on the GPU race on it: serialise
+ *     them, e.g. on one stream.
+ *   q, dtype, vol, stream: as for lamino_backproject_fourier.
+ */
+int lamino_backproject_fourier_noalloc(lamino_plan_t plan, const void* q, int dtype, float* vol,
+                                       cudaStream_t stream);
+
+/*
  * lamino_fbp -- filtered backprojection (Eq. recon): lamino_filter followed by
  * the chosen backprojection form. For LAMINO_FOURIER the filter is fused into
  * the first FFT pass; for LAMINO_DIRECT the filtered rows go through a plan

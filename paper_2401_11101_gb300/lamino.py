@@ -29,7 +29,7 @@ FORMS = {"direct": DIRECT, "fourier": FOURIER}
 
 # every symbol include/lamino.h declares
 EXPORTS = ("lamino_plan", "lamino_get_info", "lamino_filter", "lamino_backproject_direct",
-           "lamino_backproject_fourier", "lamino_fbp", "lamino_fbp_host", "lamino_project",
+           "lamino_backproject_fourier", "lamino_backproject_fourier_noalloc", "lamino_fbp", "lamino_fbp_host", "lamino_project",
            "lamino_status", "lamino_profile", "lamino_profile_read", "lamino_workspace_bytes",
            "lamino_last_error", "lamino_destroy")
 
@@ -74,6 +74,7 @@ def load_library(path: str = LIB_PATH):
     lib.lamino_filter.argtypes = [vp, vp, ci, vp, ci, vp]
     lib.lamino_backproject_direct.argtypes = [vp, vp, vp, vp]
     lib.lamino_backproject_fourier.argtypes = [vp, vp, ci, vp, vp]
+    lib.lamino_backproject_fourier_noalloc.argtypes = [vp, vp, ci, vp, vp]
     lib.lamino_fbp.argtypes = [vp, ci, vp, ci, vp, ci, vp]
     lib.lamino_fbp_host.argtypes = [vp, ci, vp, ci, vp, ci, vp]
     lib.lamino_project.argtypes = [vp, ci, vp, vp, vp]
@@ -163,6 +164,16 @@ class Plan:
         v = self._out(out, self.shape_vol)
         self._check(self._lib.lamino_backproject_fourier(self._h, q.data_ptr(), DTYPES[q.dtype],
                                                          v.data_ptr(), _stream(self.device)))
+        return v
+
+    def backproject_fourier_noalloc(self, q, out):
+        """Fourier-form backprojection that allocates no device memory (its
+        workspace is the library's fixed 64 MiB static array). `out` must be
+        given, since creating it would allocate."""
+        q = self._tensor(q, self.shape_proj, tuple(DTYPES), "q")
+        v = self._tensor(out, self.shape_vol, (torch.float32,), "out")
+        self._check(self._lib.lamino_backproject_fourier_noalloc(
+            self._h, q.data_ptr(), DTYPES[q.dtype], v.data_ptr(), _stream(self.device)))
         return v
 
     def backproject(self, q, form="fourier", out=None):
