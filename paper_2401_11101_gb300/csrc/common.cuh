@@ -27,8 +27,8 @@ struct FftDesc {
     const float2* tw = nullptr;  // device table exp(-2 pi i s/n), s in [0, n)
 };
 
-// Elements per thread: 16 for 2^k lengths (radix-8/4 stages), 12 for 3*2^k
-// lengths (radix-4/2 stages and one radix-3 stage); both fit in registers.
+// Elements per thread: 8 for 2^k lengths (radix-8 stages, one radix-4/2), 12
+// for 3*2^k lengths (radix-4/2 stages and one radix-3 stage).
 int fft_elems(int n);
 bool fft_len_ok(int n);
 int fft_size_at_least(double n);   // smallest 2^k or 3*2^k >= n
@@ -271,7 +271,8 @@ __device__ __forceinline__ void fft_run(S x, const FftDesc& f, int tid, bool act
         const int R = (f.rads >> (4 * st)) & 15u;
         if constexpr (E % 8 == 0) {
             if (R == 8) fft_stage<E, 8>(x, f, tid, active, ns, s);
-            else fft_stage<E, 4>(x, f, tid, active, ns, s);
+            else if (R == 4) fft_stage<E, 4>(x, f, tid, active, ns, s);
+            else fft_stage<E, 2>(x, f, tid, active, ns, s);
         } else {
             if (R == 4) fft_stage<E, 4>(x, f, tid, active, ns, s);
             else if (R == 2) fft_stage<E, 2>(x, f, tid, active, ns, s);

@@ -142,9 +142,9 @@ int filter_typed(lamino_plan_t p, const Tin* d, float* q, int kind, cudaStream_t
     dim3 grid((unsigned)((npairs + pairs - 1) / pairs));
     const float* filt = p->d_filt + (size_t)kind * p->Wp;
     ProfScope prof(p, "filter", s);
-    if (f.e == 16) {
-        cudaFuncSetAttribute(k_filter<16, Tin>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-        k_filter<16, Tin><<<grid, pairs * f.t, smem, s>>>(d, q, nrows, p->W, f, filt, pairs);
+    if (f.e == 8) {
+        cudaFuncSetAttribute(k_filter<8, Tin>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        k_filter<8, Tin><<<grid, pairs * f.t, smem, s>>>(d, q, nrows, p->W, f, filt, pairs);
     } else {
         cudaFuncSetAttribute(k_filter<12, Tin>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         k_filter<12, Tin><<<grid, pairs * f.t, smem, s>>>(d, q, nrows, p->W, f, filt, pairs);
@@ -177,13 +177,13 @@ int rowfft_typed(lamino_plan_t p, const Tin* d, float2* R, int kind, cudaStream_
     const float* filt = kind >= 0 ? p->d_filt + (size_t)kind * p->Wp : nullptr;
     const int ef = p->fWf.e;
     if (kind < 0) {
-        return ef == 16 ? rowfft_launch<0, 16, Tin>(p, d, R, filt, s)
+        return ef == 8 ? rowfft_launch<0, 8, Tin>(p, d, R, filt, s)
                         : rowfft_launch<0, 12, Tin>(p, d, R, filt, s);
     }
     const int ep = p->fWp.e;
-    if (ep == 16 && ef == 16) return rowfft_launch<16, 16, Tin>(p, d, R, filt, s);
-    if (ep == 16 && ef == 12) return rowfft_launch<16, 12, Tin>(p, d, R, filt, s);
-    if (ep == 12 && ef == 16) return rowfft_launch<12, 16, Tin>(p, d, R, filt, s);
+    if (ep == 8 && ef == 8) return rowfft_launch<8, 8, Tin>(p, d, R, filt, s);
+    if (ep == 8 && ef == 12) return rowfft_launch<8, 12, Tin>(p, d, R, filt, s);
+    if (ep == 12 && ef == 8) return rowfft_launch<12, 8, Tin>(p, d, R, filt, s);
     return rowfft_launch<12, 12, Tin>(p, d, R, filt, s);
 }
 

@@ -182,6 +182,30 @@ __device__ __forceinline__ int block_scan(int* v, int n, int* tmp) {
 constexpr float kRoundMagic = 12582912.0f;   // 1.5 * 2^23
 constexpr int kRoundMagicBits = 0x4B400000;  // its bit pattern
 
+// Shared-memory int32 reduction at a byte offset known at compile time.
+template <int OFF>
+__device__ __forceinline__ void red_s32(uint32_t addr, int v) {
+    asm volatile("red.shared.add.s32 [%0+%2], %1;" ::"r"(addr), "r"(v), "n"(OFF) : "memory");
+}
+__device__ __forceinline__ int round_to_int(float a, float b) {
+    return __float_as_int(fmaf(a, b, kRoundMagic)) - kRoundMagicBits;
+}
+// The 2W taps of one point row: consecutive cells starting at byte address bre
+// (real plane) and bim (imaginary plane).
+template <int C, int N>
+struct TapRow {
+    static __device__ __forceinline__ void run(uint32_t bre, uint32_t bim, float vr, float vi,
+                                               const float (&gx)[N]) {
+        red_s32<4 * C>(bre, round_to_int(vr, gx[C]));
+        red_s32<4 * C>(bim, round_to_int(vi, gx[C]));
+        TapRow<C + 1, N>::run(bre, bim, vr, vi, gx);
+    }
+};
+template <int N>
+struct TapRow<N, N> {
+    static __device__ __forceinline__ void run(uint32_t, uint32_t, float, float, const float (&)[N]) {}
+};
+
 template <int E, int W>
 __global__ void __launch_bounds__(768, 1) k_grid(GridArgs a) {
     extern __shared__ float smf[];
@@ -284,6 +308,8 @@ __global__ void __launch_bounds__(768, 1) k_grid(GridArgs a) {
     const float q = (S1 > 0.f) ? fminf(1073741824.0f / S1, 2097152.0f / Smax) : 1.0f;
 
     // pass 2: spread
+    const uint32_t s_re = (uint32_t)__cvta_generic_to_shared(Ui_re);
+    const uint32_t plane_bytes = 4u * (uint32_t)(T2 * ld);
     for (int base = warp * 32; base < total; base += nwarps * 32) {
         int k, m;
         if (!locate(base, k, m)) continue;
@@ -300,17 +326,13 @@ __global__ void __launch_bounds__(768, 1) k_grid(GridArgs a) {
         X -= floorf(X / M1) * M1;          // X in [0, M1]
         const float fx = floorf(X), fy = floorf(Y);
         float gx[2 * W];
-        int col[2 * W];
         const int sx0 = (int)fx - W + 1;
 #pragma unroll
         for (int c = 0; c < 2 * W; ++c) {
             const float dx = fx - W + 1 + c - X;
             gx[c] = __expf(a.c1 * dx * dx);
-            int s1 = sx0 + c;
-            s1 += (s1 < 0) ? M1 : 0;
-            s1 -= (s1 >= M1) ? M1 : 0;
-            col[c] = s1;
         }
+        const bool wraps = sx0 < 0 || sx0 + 2 * W > M1;   // rare: within W of the grid edge
         // rows of the point: s2 = fy - W + 1 + jy; band row rr = s2 - s20 (mod M2)
         int r0 = (int)fy - W + 1 - s20;                 // in (-2 M2 - W, M2)
         r0 += (r0 < 0) ? M2 : 0;
@@ -323,12 +345,19 @@ __global__ void __launch_bounds__(768, 1) k_grid(GridArgs a) {
             const float dy = (float)((int)fy - W + 1 + jy) - Y;
             const float gy = __expf(a.c2 * dy * dy);
             const float vr = g.x * gy, vi = g.y * gy;
-            int* rre = Ui_re + rr * ld;
-            int* rim = Ui_im + rr * ld;
+            const uint32_t row = s_re + 4u * (uint32_t)(rr * ld);
+            if (!wraps) {
+                const uint32_t b = row + 4u * (uint32_t)sx0;
+                TapRow<0, 2 * W>::run(b, b + plane_bytes, vr, vi, gx);
+            } else {
 #pragma unroll
-            for (int c = 0; c < 2 * W; ++c) {
-                atomicAdd(rre + col[c], __float_as_int(fmaf(vr, gx[c], kRoundMagic)) - kRoundMagicBits);
-                atomicAdd(rim + col[c], __float_as_int(fmaf(vi, gx[c], kRoundMagic)) - kRoundMagicBits);
+                for (int c = 0; c < 2 * W; ++c) {
+                    int s1 = sx0 + c;
+                    s1 += (s1 < 0) ? M1 : 0;
+                    s1 -= (s1 >= M1) ? M1 : 0;
+                    red_s32<0>(row + 4u * (uint32_t)s1, round_to_int(vr, gx[c]));
+                    red_s32<0>(row + plane_bytes + 4u * (uint32_t)s1, round_to_int(vi, gx[c]));
+                }
             }
         }
     }
@@ -488,9 +517,9 @@ int run_fourier_after_rows(lamino_plan_t p, float* vol, cudaStream_t s) {
         dim3 grid(p->Wf / C, p->nproj);
         int threads = std::min(512, std::max(C * f.t, 128));
         ProfScope prof(p, "colfft", s);
-        if (f.e == 16) {
-            set_smem(k_colfft<16>, smem);
-            k_colfft<16><<<grid, threads, smem, s>>>(R, G, p->nproj, p->H, p->Wf, p->L, p->offv, f, p->d_phv, C);
+        if (f.e == 8) {
+            set_smem(k_colfft<8>, smem);
+            k_colfft<8><<<grid, threads, smem, s>>>(R, G, p->nproj, p->H, p->Wf, p->L, p->offv, f, p->d_phv, C);
         } else {
             set_smem(k_colfft<12>, smem);
             k_colfft<12><<<grid, threads, smem, s>>>(R, G, p->nproj, p->H, p->Wf, p->L, p->offv, f, p->d_phv, C);
@@ -524,22 +553,24 @@ int run_fourier_after_rows(lamino_plan_t p, float* vol, cudaStream_t s) {
         int threads = 768;
         dim3 grid(p->M2 / T2, p->L);
         ProfScope prof(p, "grid", s);
-        if (p->fM1.e == 16) dispatch_grid_w<16>(p->w, a, grid, threads, smem, s);
+        if (p->fM1.e == 8) dispatch_grid_w<8>(p->w, a, grid, threads, smem, s);
         else dispatch_grid_w<12>(p->w, a, grid, threads, smem, s);
         LAM_LAUNCH_CHECK(p, "gridding kernel");
     }
     // x2 inverse FFT
     {
         const FftDesc& f = p->fM2;
+        // <= ~72 KB per block so that several blocks share an SM and one
+        // block's loads overlap another's FFT
         int C = 16;
-        while (C > 1 && (size_t)C * (f.n + 1) * sizeof(float2) > 132 * 1024) C /= 2;
+        while (C > 1 && (size_t)C * (f.n + 1) * sizeof(float2) > 72 * 1024) C /= 2;
         size_t smem = (size_t)C * (f.n + 1) * sizeof(float2);
         dim3 grid((p->n0 + C - 1) / C, p->L);
         int threads = std::min(512, std::max(128, C * f.t));
         ProfScope prof(p, "colifft", s);
-        if (f.e == 16) {
-            set_smem(k_colifft<16>, smem);
-            k_colifft<16><<<grid, threads, smem, s>>>(V, P, p->n0, p->n1, f, p->d_dec2, C);
+        if (f.e == 8) {
+            set_smem(k_colifft<8>, smem);
+            k_colifft<8><<<grid, threads, smem, s>>>(V, P, p->n0, p->n1, f, p->d_dec2, C);
         } else {
             set_smem(k_colifft<12>, smem);
             k_colifft<12><<<grid, threads, smem, s>>>(V, P, p->n0, p->n1, f, p->d_dec2, C);
@@ -551,14 +582,14 @@ int run_fourier_after_rows(lamino_plan_t p, float* vol, cudaStream_t s) {
         const FftDesc& f = p->fM3;
         int C = 16;
         auto bytes = [&](int c) { return (size_t)c * ((size_t)p->L + f.n + 1) * sizeof(float2); };
-        while (C > 1 && bytes(C) > 132 * 1024) C /= 2;
+        while (C > 1 && bytes(C) > 72 * 1024) C /= 2;
         size_t smem = bytes(C);
         dim3 grid((p->n0 + C - 1) / C, p->n1);
         int threads = std::min(512, std::max(128, C * f.t));
         ProfScope prof(p, "zusfft", s);
-        if (f.e == 16) {
-            set_smem(k_zusfft<16>, smem);
-            k_zusfft<16><<<grid, threads, smem, s>>>(P, vol, p->L, p->n0, p->n1, p->n2, f, p->d_zoff,
+        if (f.e == 8) {
+            set_smem(k_zusfft<8>, smem);
+            k_zusfft<8><<<grid, threads, smem, s>>>(P, vol, p->L, p->n0, p->n1, p->n2, f, p->d_zoff,
                                                      p->d_zl, p->d_zw, p->d_dec3, C);
         } else {
             set_smem(k_zusfft<12>, smem);

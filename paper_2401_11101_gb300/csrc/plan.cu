@@ -98,11 +98,11 @@ void prof_end(lamino_plan_t p, cudaStream_t s) {
     p->recs.back().b = p->ev_used - 1;
 }
 
-int fft_elems(int n) { return (n % 3 == 0) ? 12 : 16; }
+int fft_elems(int n) { return (n % 3 == 0) ? 12 : 8; }
 
 bool fft_len_ok(int n) {
     if (n <= 0 || n > kMaxFft) return false;
-    if (is_pow2(n)) return n >= 16;
+    if (is_pow2(n)) return n >= 8;
     return n % 3 == 0 && is_pow2(n / 3) && n >= 12;
 }
 
@@ -122,9 +122,9 @@ using namespace lam;
 
 namespace {
 
-// Radix schedule. 2^k (k >= 4, 16 elements per thread): radix-8 stages and
-// one or two radix-4 stages (k = 3a + 2b). 3*2^k (k >= 2, 12 per thread):
-// radix-4 stages, a radix-2 stage if k is odd, then one radix-3 stage.
+// Radix schedule. 2^k (k >= 3, 8 elements per thread): radix-8 stages and one
+// radix-4 or radix-2 stage for k mod 3 = 2 or 1. 3*2^k (k >= 2, 12 per
+// thread): radix-4 stages, a radix-2 stage if k is odd, then one radix-3 stage.
 FftDesc make_desc(int n) {
     FftDesc f;
     f.n = n;
@@ -138,9 +138,9 @@ FftDesc make_desc(int n) {
         if (k == 1) push(2);
         push(3);
     } else {
-        int fours = (3 - k % 3) % 3;     // k - 2*fours must be a multiple of 3
-        for (int i = 0; i < (k - 2 * fours) / 3; ++i) push(8);
-        for (int i = 0; i < fours; ++i) push(4);
+        for (int i = 0; i < k / 3; ++i) push(8);
+        if (k % 3 == 2) push(4);
+        if (k % 3 == 1) push(2);
     }
     return f;
 }
