@@ -67,6 +67,7 @@ struct lamino_plan_s {
     int* d_zoff = nullptr;         // [M3+1] CSR offsets of the x3 gridding table
     int* d_zl = nullptr;           // taps: plane index
     float* d_zw = nullptr;         // taps: weight (Gaussian x Hermitian factor)
+    int2* d_ztap = nullptr;        // [L][2 wz] (cell, weight bits) per plane: the same taps by plane
     float2* d_tw = nullptr;        // all FFT twiddle tables
     int* d_err = nullptr;          // device error word (bounded waits)
 
@@ -133,6 +134,7 @@ int launch_rowfft(lamino_plan_t p, const void* d, int dtype, float2* R, int kind
 int run_fourier_after_rows(lamino_plan_t p, float* vol, cudaStream_t s);
 int launch_direct(lamino_plan_t p, const float* q, float* vol, cudaStream_t s);
 int launch_project_direct(lamino_plan_t p, const float* vol, float* d, cudaStream_t s);
+int launch_project_fourier(lamino_plan_t p, const float* vol, float* d, cudaStream_t s);
 int fourier_workspace(lamino_plan_t p, size_t* a_bytes, size_t* b_bytes);
 
 // device helpers --------------------------------------------------------------

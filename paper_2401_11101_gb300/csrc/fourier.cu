@@ -182,6 +182,73 @@ __device__ __forceinline__ int block_scan(int* v, int n, int* tmp) {
 constexpr float kRoundMagic = 12582912.0f;   // 1.5 * 2^23
 constexpr int kRoundMagicBits = 0x4B400000;  // its bit pattern
 
+// The band's points, as a compact list of non-empty m-intervals over all lines:
+// every line k contributes the m in [-Wf/2 + 1, Wf/2 - 1] with Y(m) inside
+// [lo, hi) (mod M2) (band_intervals). ioff[i] = first point number of interval
+// i, ikm[i] = (k << 13) | (m start + 4096), ioff[nintv] = total. lcnt is
+// [nproj] scratch. Whole block; returns the number of points.
+__device__ __forceinline__ int band_list(const float2* __restrict__ trig, int nproj, int Wf, int M2,
+                                         float rho, float lo, float hi, int* ioff, int* ikm,
+                                         int* lcnt, int* scan_tmp, int& nintv_out) {
+    const int half = Wf / 2;
+    const int per = (nproj + blockDim.x - 1) / blockDim.x;   // lines per thread (<= 4)
+    int ms[4][4], me[4][4], nint[4];
+#pragma unroll
+    for (int t = 0; t < 4; ++t) {
+        nint[t] = 0;
+        const int k = threadIdx.x * per + t;
+        if (t < per && k < nproj) {
+            const float2 cs = __ldg(trig + k);
+            const float AY = (float)M2 * cs.y / (float)Wf, BY = -(float)M2 * rho * cs.x;
+            nint[t] = band_intervals(AY, BY, -half + 1, half - 1, lo, hi, M2, ms[t], me[t]);
+            lcnt[k] = nint[t];
+        }
+    }
+    __syncthreads();
+    const int nintv = block_scan(lcnt, nproj, scan_tmp);
+#pragma unroll
+    for (int t = 0; t < 4; ++t) {
+        const int k = threadIdx.x * per + t;
+        if (t < per && k < nproj) {
+            const int o = lcnt[k];
+            for (int i = 0; i < nint[t]; ++i) {
+                ioff[o + i] = me[t][i] - ms[t][i] + 1;
+                ikm[o + i] = (k << 13) | (ms[t][i] + 4096);
+            }
+        }
+    }
+    __syncthreads();
+    const int total = block_scan(ioff, nintv, scan_tmp);
+    if (threadIdx.x == 0) ioff[nintv] = total;
+    __syncthreads();
+    nintv_out = nintv;
+    return total;
+}
+
+// Point number base + lane of a band list -> (line k, m); lane 0 finds the
+// interval of `base` by bisection and every lane steps forward from it. Must be
+// called by the whole warp; false for lanes past the end.
+__device__ __forceinline__ bool band_locate(const int* ioff, const int* ikm, int nintv, int total,
+                                            int base, int lane, int& k, int& m) {
+    int iv = 0;
+    if (lane == 0) {
+        int a0 = 0, b0 = nintv;   // ioff[a0] <= base < ioff[b0]
+        while (b0 - a0 > 1) {
+            const int mid = (a0 + b0) >> 1;
+            if (ioff[mid] <= base) a0 = mid; else b0 = mid;
+        }
+        iv = a0;
+    }
+    iv = __shfl_sync(0xffffffffu, iv, 0);
+    const int p = base + lane;
+    if (p >= total) return false;
+    while (ioff[iv + 1] <= p) ++iv;
+    const int km = ikm[iv];
+    k = km >> 13;
+    m = (km & 8191) - 4096 + (p - ioff[iv]);
+    return true;
+}
+
 // Shared-memory int32 reduction at a byte offset known at compile time.
 template <int OFF>
 __device__ __forceinline__ void red_s32(uint32_t addr, int v) {
@@ -230,59 +297,11 @@ __global__ void __launch_bounds__(768, 1) k_grid(GridArgs a) {
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
     const int half = a.Wf / 2;
     // points whose 2W rows reach the band: Y in [s20 - W, s20 + T2 + W - 1)
-    const float lo = (float)(s20 - W), hi = (float)(s20 + T2 + W - 1);
-    // one thread per line: its intervals stay in registers across the scans
-    const int per = (nproj + blockDim.x - 1) / blockDim.x;   // lines per thread (<= 4)
-    int ms[4][4], me[4][4], nint[4];
-#pragma unroll
-    for (int t = 0; t < 4; ++t) {
-        nint[t] = 0;
-        const int k = threadIdx.x * per + t;
-        if (t < per && k < nproj) {
-            const float2 cs = __ldg(a.trig + k);
-            const float AY = (float)M2 * cs.y / (float)a.Wf, BY = -(float)M2 * rho * cs.x;
-            nint[t] = band_intervals(AY, BY, -half + 1, half - 1, lo, hi, M2, ms[t], me[t]);
-            lcnt[k] = nint[t];
-        }
-    }
-    __syncthreads();
-    const int nintv = block_scan(lcnt, nproj, scan_tmp);
-#pragma unroll
-    for (int t = 0; t < 4; ++t) {
-        const int k = threadIdx.x * per + t;
-        if (t < per && k < nproj) {
-            int o = lcnt[k];
-            for (int i = 0; i < nint[t]; ++i) {
-                ioff[o + i] = me[t][i] - ms[t][i] + 1;
-                ikm[o + i] = (k << 13) | (ms[t][i] + 4096);
-            }
-        }
-    }
-    __syncthreads();
-    const int total = block_scan(ioff, nintv, scan_tmp);
-    if (threadIdx.x == 0) ioff[nintv] = total;
-    __syncthreads();
-
-    // A warp takes 32 consecutive point numbers: lane 0 finds the interval of
-    // the first one, every lane then steps forward from it.
+    int nintv = 0;
+    const int total = band_list(a.trig, nproj, a.Wf, M2, rho, (float)(s20 - W),
+                                (float)(s20 + T2 + W - 1), ioff, ikm, lcnt, scan_tmp, nintv);
     auto locate = [&](int base, int& k, int& m) -> bool {
-        int iv = 0;
-        if (lane == 0) {
-            int a0 = 0, b0 = nintv;   // ioff[a0] <= base < ioff[b0]
-            while (b0 - a0 > 1) {
-                const int mid = (a0 + b0) >> 1;
-                if (ioff[mid] <= base) a0 = mid; else b0 = mid;
-            }
-            iv = a0;
-        }
-        iv = __shfl_sync(0xffffffffu, iv, 0);
-        const int p = base + lane;
-        if (p >= total) return false;
-        while (ioff[iv + 1] <= p) ++iv;
-        const int km = ikm[iv];
-        k = km >> 13;
-        m = (km & 8191) - 4096 + (p - ioff[iv]);
-        return true;
+        return band_locate(ioff, ikm, nintv, total, base, lane, k, m);
     };
 
     const float2* Gl = a.G + (size_t)l * nproj * a.Wf;
@@ -474,6 +493,214 @@ void set_smem(K kern, size_t smem) {
     cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
 }
 
+
+// ============================================================================
+// Transpose of the Fourier-form backprojection (the forward operator of
+// Eq. fftfwd in this discretisation). Every stage is the conjugate transpose
+// of its forward stage, in reverse order; the gridding becomes interpolation
+// (a gather: no atomics), the inverse FFTs become forward FFTs and vice versa.
+// ============================================================================
+
+// x3: vol column -> x dec3, embed, forward FFT, gather each plane's 2wz taps.
+template <int E>
+__global__ void __launch_bounds__(512, 2) k_zusfft_t(const float* __restrict__ vol, float2* __restrict__ Pt,
+                                                     int L, int n0, int n1, int n2, FftDesc f3,
+                                                     const int2* __restrict__ ztap, int wz,
+                                                     const float* __restrict__ dec3, int C) {
+    extern __shared__ float2 sm[];
+    const int M3 = f3.n, ld = M3 + 1;
+    const int i1 = blockIdx.y, i00 = blockIdx.x * C;
+    for (int i = threadIdx.x; i < C * ld; i += blockDim.x) sm[i] = make_float2(0.f, 0.f);
+    __syncthreads();
+    for (int idx = threadIdx.x; idx < C * n2; idx += blockDim.x) {
+        const int c = idx % C, i2 = idx / C, i0 = i00 + c;
+        int s3 = i2 - n2 / 2;
+        s3 += (s3 < 0) ? M3 : 0;
+        const float v = (i0 < n0) ? vol[((size_t)i2 * n1 + i1) * n0 + i0] * __ldg(dec3 + i2) : 0.f;
+        sm[c * ld + s3] = make_float2(v, 0.f);
+    }
+    __syncthreads();
+    fft_many<E>(sm, ld, C, f3, -1.f);
+    for (int idx = threadIdx.x; idx < C * L; idx += blockDim.x) {
+        const int c = idx % C, l = idx / C, i0 = i00 + c;
+        if (i0 >= n0) continue;
+        float2 acc = make_float2(0.f, 0.f);
+        for (int t = 0; t < 2 * wz; ++t) {
+            const int2 tp = __ldg(ztap + (size_t)l * 2 * wz + t);
+            const float w = __int_as_float(tp.y);
+            const float2 u = sm[c * ld + tp.x];
+            acc.x = fmaf(w, u.x, acc.x);
+            acc.y = fmaf(w, u.y, acc.y);
+        }
+        Pt[((size_t)l * n1 + i1) * n0 + i0] = acc;
+    }
+}
+
+// x2: column of plane l at x1 -> x dec2, embed, forward FFT -> Vt[l][x1][s2].
+template <int E>
+__global__ void __launch_bounds__(512, 2) k_colifft_t(const float2* __restrict__ Pt, float2* __restrict__ Vt,
+                                                      int n0, int n1, FftDesc f2,
+                                                      const float* __restrict__ dec2, int C) {
+    extern __shared__ float2 sm[];
+    const int M2 = f2.n, ld = M2 + 1;
+    const int l = blockIdx.y, i00 = blockIdx.x * C;
+    for (int i = threadIdx.x; i < C * ld; i += blockDim.x) sm[i] = make_float2(0.f, 0.f);
+    __syncthreads();
+    for (int idx = threadIdx.x; idx < C * n1; idx += blockDim.x) {
+        const int c = idx % C, i1 = idx / C, i0 = i00 + c;
+        int s2 = i1 - n1 / 2;
+        s2 += (s2 < 0) ? M2 : 0;
+        sm[c * ld + s2] = (i0 < n0) ? cscale(Pt[((size_t)l * n1 + i1) * n0 + i0], __ldg(dec2 + i1))
+                                    : make_float2(0.f, 0.f);
+    }
+    __syncthreads();
+    fft_many<E>(sm, ld, C, f2, -1.f);
+    for (int idx = threadIdx.x; idx < C * M2; idx += blockDim.x) {
+        const int c = idx / M2, s = idx % M2, i0 = i00 + c;
+        if (i0 < n0) Vt[((size_t)l * n0 + i0) * M2 + s] = sm[c * ld + s];
+    }
+}
+
+// Gridding transpose: CTA = (plane l, band of T2 rows) + a halo of 2W - 1 rows
+// below it. Each row s2: x dec1, embed along s1, forward FFT; then every point
+// whose first tap row lies in the band (each point has exactly one such band)
+// gathers its (2W)^2 taps.
+template <int E, int W>
+__global__ void __launch_bounds__(512, 1) k_grid_t(GridArgs a, const float2* __restrict__ Vt,
+                                                   float2* __restrict__ Gt) {
+    extern __shared__ float2 smx[];
+    const int M1 = a.M1, M2 = a.M2, T2 = a.T2, ld = a.ld, NR = T2 + 2 * W - 1;
+    const int nproj = a.nproj, n0 = a.n0;
+    float2* X = smx;                                           // [NR][ld]
+    int* ioff = reinterpret_cast<int*>(X + (size_t)NR * ld);
+    int* ikm = ioff + 4 * nproj + 1;
+    int* lcnt = ikm + 4 * nproj;
+    __shared__ int scan_tmp[32];
+    const int band = blockIdx.x, l = blockIdx.y, s20 = band * T2;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
+    const int half = a.Wf / 2;
+    for (int i = threadIdx.x; i < NR * ld; i += blockDim.x) X[i] = make_float2(0.f, 0.f);
+    __syncthreads();
+    for (int idx = threadIdx.x; idx < NR * n0; idx += blockDim.x) {
+        const int rr = idx % NR, i0 = idx / NR;
+        int s2 = s20 + rr;
+        s2 -= (s2 >= M2) ? M2 : 0;
+        int s1 = i0 - n0 / 2;
+        s1 += (s1 < 0) ? M1 : 0;
+        X[rr * ld + s1] = cscale(Vt[((size_t)l * n0 + i0) * M2 + s2], __ldg(a.dec1 + i0));
+    }
+    __syncthreads();
+    fft_many<E>(X, ld, NR, a.f1, -1.f);
+
+    const float rho = (float)l * a.sinphi / (float)a.Hf;
+    // owners: first tap row fy - W + 1 in [s20, s20 + T2), i.e. Y in [s20 + W - 1, s20 + T2 + W - 1)
+    int nintv = 0;
+    const int total = band_list(a.trig, nproj, a.Wf, M2, rho, (float)(s20 + W - 1),
+                                (float)(s20 + T2 + W - 1), ioff, ikm, lcnt, scan_tmp, nintv);
+    float2* Gl = Gt + (size_t)l * nproj * a.Wf;
+    if (band == 0)   // the dropped Nyquist column m = -Wf/2
+        for (int k = threadIdx.x; k < nproj; k += blockDim.x) Gl[(size_t)k * a.Wf] = make_float2(0.f, 0.f);
+    for (int base = warp * 32; base < total; base += nwarps * 32) {
+        int k, m;
+        if (!band_locate(ioff, ikm, nintv, total, base, lane, k, m)) continue;
+        const float2 cs = __ldg(a.trig + k);
+        const float AX = (float)M1 * cs.x / (float)a.Wf, BX = (float)M1 * rho * cs.y;
+        const float AY = (float)M2 * cs.y / (float)a.Wf, BY = -(float)M2 * rho * cs.x;
+        float X0 = fmaf(AX, (float)m, BX);
+        const float Y = fmaf(AY, (float)m, BY);
+        X0 -= floorf(X0 / M1) * M1;
+        const float fx = floorf(X0), fy = floorf(Y);
+        int r0 = (int)fy - W + 1 - s20;
+        r0 += (r0 < 0) ? M2 : 0;
+        r0 += (r0 < 0) ? M2 : 0;
+        r0 -= (r0 >= M2) ? M2 : 0;
+        if (r0 >= T2) continue;                 // owned by another band
+        float gx[2 * W];
+        int col[2 * W];
+        const int sx0 = (int)fx - W + 1;
+#pragma unroll
+        for (int c = 0; c < 2 * W; ++c) {
+            const float dx = fx - W + 1 + c - X0;
+            gx[c] = __expf(a.c1 * dx * dx);
+            int s1 = sx0 + c;
+            s1 += (s1 < 0) ? M1 : 0;
+            s1 -= (s1 >= M1) ? M1 : 0;
+            col[c] = s1;
+        }
+        float2 acc = make_float2(0.f, 0.f);
+#pragma unroll
+        for (int jy = 0; jy < 2 * W; ++jy) {
+            const float dy = (float)((int)fy - W + 1 + jy) - Y;
+            const float gy = __expf(a.c2 * dy * dy);
+            const float2* row = X + (size_t)(r0 + jy) * ld;
+            float2 racc = make_float2(0.f, 0.f);
+#pragma unroll
+            for (int c = 0; c < 2 * W; ++c) {
+                const float2 u = row[col[c]];
+                racc.x = fmaf(gx[c], u.x, racc.x);
+                racc.y = fmaf(gx[c], u.y, racc.y);
+            }
+            acc.x = fmaf(gy, racc.x, acc.x);
+            acc.y = fmaf(gy, racc.y, acc.y);
+        }
+        Gl[(size_t)k * a.Wf + (m + half)] = acc;
+    }
+}
+
+// Column pass transpose: plane values of one (projection, column) x conj(phase)
+// -> inverse FFT over l (only l < Hf/2 non-zero) -> detector rows.
+template <int E>
+__global__ void __launch_bounds__(512, 2) k_colfft_t(const float2* __restrict__ Gt, float2* __restrict__ Rt,
+                                                     int nproj, int H, int Wf, int L, int offv, FftDesc fh,
+                                                     const float2* __restrict__ phv, int C) {
+    extern __shared__ float2 sm[];
+    const int Hf = fh.n, ld = Hf + 1;
+    const int k = blockIdx.y, m0 = blockIdx.x * C;
+    for (int idx = threadIdx.x; idx < C * Hf; idx += blockDim.x) {
+        const int c = idx % C, l = idx / C;
+        float2 v = make_float2(0.f, 0.f);
+        if (l < L) {
+            float2 ph = __ldg(phv + l);
+            ph.y = -ph.y;
+            v = cmul(Gt[((size_t)l * nproj + k) * Wf + m0 + c], ph);
+        }
+        sm[c * ld + l] = v;
+    }
+    __syncthreads();
+    fft_many<E>(sm, ld, C, fh, +1.f);
+    for (int idx = threadIdx.x; idx < C * H; idx += blockDim.x) {
+        const int c = idx % C, r = idx / C;
+        Rt[((size_t)k * H + r) * Wf + m0 + c] = sm[c * ld + r + offv];
+    }
+}
+
+// Row pass transpose: x conj(phase), inverse FFT over m, real part at the
+// detector columns, times nproj/pi (lamino_project omits the pi/nproj weight).
+template <int E>
+__global__ void __launch_bounds__(512, 2) k_rowfft_t(const float2* __restrict__ Rt, float* __restrict__ d,
+                                                     long nrows, int W, int offu, FftDesc ff,
+                                                     const float2* __restrict__ phu, float unscale,
+                                                     int rows_per_block) {
+    extern __shared__ float2 sm[];
+    const int Nf = ff.n, T = ff.t;
+    const int seq = threadIdx.x / T, tid = threadIdx.x % T;
+    const long row = (long)blockIdx.x * rows_per_block + seq;
+    const bool active = seq < rows_per_block && row < nrows;
+    float2* x = sm + (size_t)min(seq, rows_per_block - 1) * Nf;
+    if (active)
+        for (int mi = tid; mi < Nf; mi += T) {
+            float2 ph = __ldg(phu + mi);
+            ph.y = -ph.y;
+            int m = mi - Nf / 2;
+            m += (m < 0) ? Nf : 0;
+            x[m] = cmul(Rt[(size_t)row * Nf + mi], ph);
+        }
+    __syncthreads();
+    fft_run<E>(x, ff, tid, active, +1.f);
+    if (active)
+        for (int j = tid; j < W; j += T) d[(size_t)row * W + j] = x[j + offu].x * unscale;
+}
+
 int largest_pow2_divisor_upto(int n, int cap) {
     int c = 1;
     while (c * 2 <= cap && n % (c * 2) == 0) c *= 2;
@@ -597,6 +824,120 @@ int run_fourier_after_rows(lamino_plan_t p, float* vol, cudaStream_t s) {
                                                      p->d_zl, p->d_zw, p->d_dec3, C);
         }
         LAM_LAUNCH_CHECK(p, "x3 USFFT kernel");
+    }
+    return LAMINO_OK;
+}
+
+
+int launch_project_fourier(lamino_plan_t p, const float* vol, float* d, cudaStream_t s) {
+    float2* Pt = (float2*)p->ws_b;   // [L][n1][n0]
+    float2* Vt = (float2*)p->ws_a;   // [L][n0][M2]
+    float2* Gt = (float2*)p->ws_b;   // [L][nproj][Wf]  (Pt is dead by then)
+    float2* Rt = (float2*)p->ws_a;   // [nproj][H][Wf]  (Vt is dead by then)
+    {   // x3
+        const FftDesc& f = p->fM3;
+        int C = 16;
+        while (C > 1 && (size_t)C * (f.n + 1) * sizeof(float2) > 72 * 1024) C /= 2;
+        size_t smem = (size_t)C * (f.n + 1) * sizeof(float2);
+        dim3 grid((p->n0 + C - 1) / C, p->n1);
+        int threads = std::min(512, std::max(128, C * f.t));
+        ProfScope prof(p, "zusfft_t", s);
+        if (f.e == 8) {
+            set_smem(k_zusfft_t<8>, smem);
+            k_zusfft_t<8><<<grid, threads, smem, s>>>(vol, Pt, p->L, p->n0, p->n1, p->n2, f, p->d_ztap, p->wz, p->d_dec3, C);
+        } else {
+            set_smem(k_zusfft_t<12>, smem);
+            k_zusfft_t<12><<<grid, threads, smem, s>>>(vol, Pt, p->L, p->n0, p->n1, p->n2, f, p->d_ztap, p->wz, p->d_dec3, C);
+        }
+        LAM_LAUNCH_CHECK(p, "x3 USFFT transpose kernel");
+    }
+    {   // x2
+        const FftDesc& f = p->fM2;
+        int C = 16;
+        while (C > 1 && (size_t)C * (f.n + 1) * sizeof(float2) > 72 * 1024) C /= 2;
+        size_t smem = (size_t)C * (f.n + 1) * sizeof(float2);
+        dim3 grid((p->n0 + C - 1) / C, p->L);
+        int threads = std::min(512, std::max(128, C * f.t));
+        ProfScope prof(p, "colifft_t", s);
+        if (f.e == 8) {
+            set_smem(k_colifft_t<8>, smem);
+            k_colifft_t<8><<<grid, threads, smem, s>>>(Pt, Vt, p->n0, p->n1, f, p->d_dec2, C);
+        } else {
+            set_smem(k_colifft_t<12>, smem);
+            k_colifft_t<12><<<grid, threads, smem, s>>>(Pt, Vt, p->n0, p->n1, f, p->d_dec2, C);
+        }
+        LAM_LAUNCH_CHECK(p, "x2 FFT transpose kernel");
+    }
+    {   // gridding transpose
+        GridArgs a;
+        a.G = nullptr; a.V = nullptr; a.trig = p->d_trig; a.dec1 = p->d_dec1;
+        a.nproj = p->nproj; a.Wf = p->Wf; a.Hf = p->Hf; a.n0 = p->n0; a.M1 = p->M1; a.M2 = p->M2;
+        a.sinphi = (float)sin(p->tilt);
+        a.c1 = (float)(-1.0 / (4.0 * p->t1));
+        a.c2 = (float)(-1.0 / (4.0 * p->t2));
+        a.f1 = p->fM1;
+        a.ld = p->M1 + 1;
+        if (p->nproj > 4 * 512 || p->Wf > 8192)
+            return fail(p, LAMINO_EUNSUPPORTED, "Fourier projector supports up to 2048 angles");
+        int T2 = 8;
+        while (T2 > 1 && (size_t)(T2 + 2 * p->w - 1) * a.ld * sizeof(float2) > 150 * 1024) T2 /= 2;
+        while (p->M2 % T2) T2 /= 2;
+        a.T2 = T2;
+        size_t smem = (size_t)(T2 + 2 * p->w - 1) * a.ld * sizeof(float2) + sizeof(int) * (9 * (size_t)p->nproj + 1);
+        if (smem > 220 * 1024)
+            return fail(p, LAMINO_EUNSUPPORTED, "gridding transpose tile of %zu bytes exceeds shared memory", smem);
+        dim3 grid(p->M2 / T2, p->L);
+        ProfScope prof(p, "grid_t", s);
+        auto go = [&](auto kern) {
+            set_smem(kern, smem);
+            kern<<<grid, 512, smem, s>>>(a, Vt, Gt);
+        };
+        const bool e8 = p->fM1.e == 8;
+        switch (p->w) {
+            case 2: e8 ? go(k_grid_t<8, 2>) : go(k_grid_t<12, 2>); break;
+            case 3: e8 ? go(k_grid_t<8, 3>) : go(k_grid_t<12, 3>); break;
+            case 4: e8 ? go(k_grid_t<8, 4>) : go(k_grid_t<12, 4>); break;
+            case 5: e8 ? go(k_grid_t<8, 5>) : go(k_grid_t<12, 5>); break;
+            case 6: e8 ? go(k_grid_t<8, 6>) : go(k_grid_t<12, 6>); break;
+            case 7: e8 ? go(k_grid_t<8, 7>) : go(k_grid_t<12, 7>); break;
+            default: e8 ? go(k_grid_t<8, 8>) : go(k_grid_t<12, 8>); break;
+        }
+        LAM_LAUNCH_CHECK(p, "gridding transpose kernel");
+    }
+    {   // column pass transpose
+        const FftDesc& f = p->fHf;
+        int C = largest_pow2_divisor_upto(p->Wf, 16);
+        while (C > 1 && (size_t)C * (f.n + 1) * sizeof(float2) > 100 * 1024) C /= 2;
+        size_t smem = (size_t)C * (f.n + 1) * sizeof(float2);
+        dim3 grid(p->Wf / C, p->nproj);
+        int threads = std::min(512, std::max(C * f.t, 128));
+        ProfScope prof(p, "colfft_t", s);
+        if (f.e == 8) {
+            set_smem(k_colfft_t<8>, smem);
+            k_colfft_t<8><<<grid, threads, smem, s>>>(Gt, Rt, p->nproj, p->H, p->Wf, p->L, p->offv, f, p->d_phv, C);
+        } else {
+            set_smem(k_colfft_t<12>, smem);
+            k_colfft_t<12><<<grid, threads, smem, s>>>(Gt, Rt, p->nproj, p->H, p->Wf, p->L, p->offv, f, p->d_phv, C);
+        }
+        LAM_LAUNCH_CHECK(p, "column FFT transpose kernel");
+    }
+    {   // row pass transpose
+        const FftDesc& f = p->fWf;
+        int rows = 1;
+        while (rows * 2 * f.t <= 512 && (size_t)rows * 2 * f.n * sizeof(float2) <= 64 * 1024) rows *= 2;
+        long nrows = (long)p->nproj * p->H;
+        size_t smem = (size_t)rows * f.n * sizeof(float2);
+        dim3 grid((unsigned)((nrows + rows - 1) / rows));
+        const float unscale = (float)(p->nproj / 3.14159265358979323846);
+        ProfScope prof(p, "rowfft_t", s);
+        if (f.e == 8) {
+            set_smem(k_rowfft_t<8>, smem);
+            k_rowfft_t<8><<<grid, rows * f.t, smem, s>>>(Rt, d, nrows, p->W, p->offu, f, p->d_phu, unscale, rows);
+        } else {
+            set_smem(k_rowfft_t<12>, smem);
+            k_rowfft_t<12><<<grid, rows * f.t, smem, s>>>(Rt, d, nrows, p->W, p->offu, f, p->d_phu, unscale, rows);
+        }
+        LAM_LAUNCH_CHECK(p, "row FFT transpose kernel");
     }
     return LAMINO_OK;
 }

@@ -190,7 +190,7 @@ int upload(lamino_plan_t p, T** dst, const std::vector<T>& v, const char* what) 
 
 void free_plan(lamino_plan_t p) {
     void* bufs[] = {p->d_trig, p->d_trig64, p->d_filt, p->d_phu, p->d_phv, p->d_dec1,
-                    p->d_dec2, p->d_dec3, p->d_zoff, p->d_zl, p->d_zw, p->d_tw, p->d_err,
+                    p->d_dec2, p->d_dec3, p->d_zoff, p->d_zl, p->d_zw, p->d_ztap, p->d_tw, p->d_err,
                     p->ws_a, p->ws_b, p->q_buf, p->h_in, p->h_vol};
     for (void* b : bufs)
         if (b) cudaFree(b);
@@ -287,6 +287,7 @@ int build_tables(lamino_plan_t p) {
     // the Hermitian factor c_l (1 for l = 0, 2 otherwise: planes -l are the
     // conjugates of planes l). Every cell lists its (l, weight) taps.
     std::vector<std::vector<std::pair<int, float>>> cells(p->M3);
+    std::vector<int2> ztap((size_t)p->L * 2 * p->wz);
     for (int l = 0; l < p->L; ++l) {
         double Z = (double)p->M3 * l * cos(p->tilt) / p->Hf;
         long fz = (long)floor(Z);
@@ -296,6 +297,10 @@ int build_tables(lamino_plan_t p) {
             double wgt = cl * exp(-dd * dd / (4.0 * p->t3));
             long cell = ((s % p->M3) + p->M3) % p->M3;
             cells[cell].push_back({l, (float)wgt});
+            float fw = (float)wgt;
+            int bits;
+            memcpy(&bits, &fw, sizeof bits);
+            ztap[(size_t)l * 2 * p->wz + (s - (fz - p->wz + 1))] = make_int2((int)cell, bits);
         }
     }
     std::vector<int> zoff(p->M3 + 1, 0), zl;
@@ -314,6 +319,7 @@ int build_tables(lamino_plan_t p) {
     if ((rc = upload(p, &p->d_zoff, zoff, "x3 table offsets"))) return rc;
     if ((rc = upload(p, &p->d_zl, zl, "x3 table planes"))) return rc;
     if ((rc = upload(p, &p->d_zw, zw, "x3 table weights"))) return rc;
+    if ((rc = upload(p, &p->d_ztap, ztap, "x3 table by plane"))) return rc;
     return LAMINO_OK;
 }
 
@@ -550,8 +556,14 @@ int lamino_project(lamino_plan_t p, int form, const float* vol, float* d, cudaSt
     int rc = set_device(p);
     if (rc) return rc;
     if (form == LAMINO_DIRECT) return launch_project_direct(p, vol, d, stream);
-    if (form == LAMINO_FOURIER)
-        return fail(p, LAMINO_EUNSUPPORTED, "Fourier-form projector not built yet");
+    if (form == LAMINO_FOURIER) {
+        if (!p->fourier_ok) return fail(p, LAMINO_EUNSUPPORTED, "%s", p->fourier_why.c_str());
+        size_t a, b;
+        fourier_workspace(p, &a, &b);
+        if ((rc = ensure_buffer(p, &p->ws_a, &p->ws_a_bytes, a, "Fourier workspace A"))) return rc;
+        if ((rc = ensure_buffer(p, &p->ws_b, &p->ws_b_bytes, b, "Fourier workspace B"))) return rc;
+        return launch_project_fourier(p, vol, d, stream);
+    }
     return fail(p, LAMINO_EINVAL, "unknown form %d", form);
 }
 

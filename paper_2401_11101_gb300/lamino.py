@@ -117,6 +117,7 @@ class Plan:
             raise LaminoError(rc, self._lib.lamino_last_error(None).decode())
         self.shape_vol = (n2, n1, n0)
         self.shape_proj = (nproj, det_h, det_w)
+        self.nproj = nproj
         info = _Info()
         self._check(self._lib.lamino_get_info(self._h, ctypes.byref(info)))
         self.info = {f: getattr(info, f) for f, _ in _Info._fields_}
