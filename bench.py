@@ -45,6 +45,8 @@ WORKLOADS = {
           "1% noise, Shepp-Logan",
     "c4": "256x256x128, 400 projections over 360 deg, detector 128x384, tilt 30 deg, Gaussian "
           "blobs, 0.5% noise, Shepp-Logan",
+    "c3": "2048x2048x512 slab, 1800 projections over 360 deg, detector 512x2048 stored FP16, "
+          "tilt 18 deg, 5000 ellipsoids + 2% dense spheres, Poisson 1e4 photons, Shepp-Logan",
 }
 FP32_LANES_PER_SM = 128
 N_SMS = 152
@@ -289,7 +291,7 @@ def run_ours(args, geom, d):
     peaks, peaks_src = measured_peaks()
     sm_mhz_max = float(peaks.get("sm_max_mhz", 2070.0))
     alu_peak = N_SMS * FP32_LANES_PER_SM * 2 * sm_mhz_max * 1e6 / 1e12  # TFLOP/s
-    alg = kernel_algorithmic(info, geom)
+    alg = kernel_algorithmic(info, geom, d.element_size())
     traffic = ncu_traffic(args.workload)
     kernels = {}
     total = sum(sum(v) for v in per.values())
@@ -357,6 +359,7 @@ def run_ours(args, geom, d):
         line = {"metric": METRIC, "value": value, "unit": "GVox/s", "n_gpus": ws, "steps": args.steps,
                 "warmup": args.warmup, "ms_per_step": t_f + t_d, "higher_is_better": True,
                 "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+                "storage": str(d.dtype).replace("torch.", ""),
                 "config": {"workload": f"{args.workload}: {WORKLOADS[args.workload]}",
                            "parallelism": f"replicas x{ws} (independent slabs)",
                            "l2": "inputs larger than L2 and a 256 MB L2 flush between steps",
@@ -385,7 +388,7 @@ def main():
     else:
         torch.cuda.set_device(local)
         geom, _, d = I.make_projections(args.workload, device=f"cuda:{local}")
-        d = d.contiguous()
+        d = d.to(I.storage_dtype(args.workload)).contiguous()
         run_ours(args, geom, d)
     if ws > 1:
         torch.distributed.destroy_process_group()

@@ -90,9 +90,9 @@ def _f64(a) -> np.ndarray:
     return np.ascontiguousarray(a, dtype=np.float64)
 
 
-def _theta(geom) -> np.ndarray:
-    return np.ascontiguousarray(
-        2.0 * np.pi * np.arange(geom.nproj, dtype=np.float64) / geom.nproj)
+def _theta(geom, angle_index=None) -> np.ndarray:
+    idx = np.arange(geom.nproj) if angle_index is None else np.asarray(angle_index)
+    return np.ascontiguousarray(2.0 * np.pi * idx.astype(np.float64) / geom.nproj)
 
 
 # ----------------------------------------------------------------------------
@@ -178,15 +178,20 @@ def backproject_direct(q, geom, z0: int = 0, z1: int | None = None) -> np.ndarra
     return out
 
 
-def backproject_direct_columns(q, geom, cols) -> np.ndarray:
-    """Direct backprojection on whole columns cols[c] = (i0, i1): out [ncol, n2]."""
+def backproject_direct_columns(q, geom, cols, angle_index=None) -> np.ndarray:
+    """Direct backprojection on whole columns cols[c] = (i0, i1): out [ncol, n2].
+
+    With angle_index, q holds only the projections with those indices of the
+    equispaced set of geom.nproj angles and the result is their contribution
+    (weight pi/geom.nproj): the backprojection is a sum over angles."""
     q = _f64(q)
+    nq = q.shape[0]
     cols = np.ascontiguousarray(cols, dtype=np.int32)
     out = np.zeros((cols.shape[0], geom.n2))
-    _load().orc_bp_direct_columns(_dp(q), geom.nproj, geom.det_h, geom.det_w,
-                                  _dp(_theta(geom)), float(geom.tilt), geom.n0, geom.n1,
-                                  geom.n2, _ip(cols), cols.shape[0], _dp(out))
-    return out
+    _load().orc_bp_direct_columns(_dp(q), nq, geom.det_h, geom.det_w,
+                                  _dp(_theta(geom, angle_index)), float(geom.tilt), geom.n0,
+                                  geom.n1, geom.n2, _ip(cols), cols.shape[0], _dp(out))
+    return out * (nq / geom.nproj)
 
 
 def project_direct(vol, geom) -> np.ndarray:
@@ -214,10 +219,10 @@ def _fourier_frame(geom):
 
 def fourier_spectra(q, geom):
     """2D DFT of every zero-padded projection with the Nyquist row and column
-    zeroed (the F_2D of Eq. fftadj). Returns D [nproj, Hf, Wf] complex128."""
+    zeroed (the F_2D of Eq. fftadj). Returns D [len(q), Hf, Wf] complex128."""
     q = _f64(q)
     Wf, Hf, offu, offv, _, _ = _fourier_frame(geom)
-    pad = np.zeros((geom.nproj, Hf, Wf))
+    pad = np.zeros((q.shape[0], Hf, Wf))
     pad[:, offv:offv + geom.det_h, offu:offu + geom.det_w] = q
     D = np.fft.fft2(pad, axes=(1, 2))
     D[:, Hf // 2, :] = 0.0
@@ -229,17 +234,19 @@ def _fourier_scale(geom, Wf, Hf):
     return (math.pi / geom.nproj) / (Wf * Hf)
 
 
-def backproject_fourier_columns(q, geom, cols) -> np.ndarray:
-    """Fourier-form backprojection (exact type-1 sum) on columns: out [ncol, n2]."""
+def backproject_fourier_columns(q, geom, cols, angle_index=None) -> np.ndarray:
+    """Fourier-form backprojection (exact type-1 sum) on columns: out [ncol, n2].
+    angle_index as for backproject_direct_columns."""
     Wf, Hf, _, _, joff, roff = _fourier_frame(geom)
     D = fourier_spectra(q, geom)
     Dre = np.ascontiguousarray(D.real)
     Dim = np.ascontiguousarray(D.imag)
+    del D
     cols = np.ascontiguousarray(cols, dtype=np.int32)
     out = np.zeros((cols.shape[0], geom.n2))
-    _load().orc_bp_fourier_columns(_dp(Dre), _dp(Dim), geom.nproj, Hf, Wf, joff, roff,
-                                   _dp(_theta(geom)), float(geom.tilt), geom.n0, geom.n1,
-                                   geom.n2, _ip(cols), cols.shape[0],
+    _load().orc_bp_fourier_columns(_dp(Dre), _dp(Dim), Dre.shape[0], Hf, Wf, joff, roff,
+                                   _dp(_theta(geom, angle_index)), float(geom.tilt), geom.n0,
+                                   geom.n1, geom.n2, _ip(cols), cols.shape[0],
                                    _fourier_scale(geom, Wf, Hf), _dp(out))
     return out
 

@@ -62,10 +62,11 @@ CONFIGS = {
     # 512x512x256 slab, 720 angles, detector 256x768, tilt 20; 200 ellipsoids
     "c2": dict(geom=Geometry(512, 512, 256, 720, 256, 768, math.radians(20.0)),
                phantom="ellipsoids", count=200, noise=0.01, filter="shepp", seed=2),
-    # 2048x2048x512 slab, 1800 angles, detector 512x2048 stored fp16, tilt 18
+    # 2048x2048x512 slab, 1800 angles, detector 512x2048 stored fp16, tilt 18;
+    # 5000 ellipsoids (semi-axes U[2, 48]) + 2% dense spheres, Poisson 1e4
     "c3": dict(geom=Geometry(2048, 2048, 512, 1800, 512, 2048, math.radians(18.0)),
                phantom="ellipsoids", count=5000, dense_frac=0.02, poisson=1e4,
-               filter="shepp", seed=3),
+               max_axis=48.0, filter="shepp", seed=3, storage="f16"),
     # 256x256x128, 400 angles, detector 128x384, tilt 30; blobs, 0.5% noise
     "c4": dict(geom=Geometry(256, 256, 128, 400, 128, 384, math.radians(30.0)),
                phantom="blobs", count=24, sigma=(3.0, 10.0), amp=(0.5, 1.0),
@@ -114,17 +115,19 @@ def _random_rotation(rng) -> np.ndarray:
     ])
 
 
-def ellipsoid_params(geom: Geometry, count: int, seed: int, dense_frac: float = 0.0):
+def ellipsoid_params(geom: Geometry, count: int, seed: int, dense_frac: float = 0.0,
+                     max_axis: float | None = None):
     """Random ellipsoids {|M(x-c)| <= 1} of density rho, overlapping densities add.
 
-    Semi-axes U[2, n/8] voxels (n = smallest of n0, n1, capped so they fit the
-    slab), random orientation, centres inside the slab, rho ~ U[0, 1]. With
+    Semi-axes U[2, n/8] voxels (n = smallest of n0, n1, or U[2, max_axis]; capped
+    so they fit the slab), random orientation, centres inside the slab,
+    rho ~ U[0, 1]. With
     dense_frac > 0 that fraction of extra small dense spheres (rho = 5) is added.
     Returns dict(M [count,3,3], centre [count,3], rho [count]).
     """
     rng = np.random.default_rng(seed)
     nmin = min(geom.n0, geom.n1)
-    amax = max(2.5, nmin / 8.0)
+    amax = max(2.5, nmin / 8.0) if max_axis is None else max_axis
     half = np.array([geom.n0, geom.n1, geom.n2], dtype=np.float64) / 2.0
     Ms, cs, rhos = [], [], []
     for _ in range(count):
@@ -211,6 +214,65 @@ def project(params: dict, geom: Geometry, device: str = "cpu", dtype=None,
     return out
 
 
+def project_boxed(params: dict, geom: Geometry, device: str = "cpu", dtype=None,
+                  angle_chunk: int = 32, batch: int = 64) -> "torch.Tensor":
+    """The same line integrals as `project` for an ellipsoid phantom, evaluated
+    only inside each ellipsoid's projected bounding disk (radius = its largest
+    semi-axis): identical values at a cost set by the footprints rather than
+    by the whole detector. Ellipsoids are processed in batches of similar size.
+    """
+    if params["kind"] != "ellipsoids":
+        return project(params, geom, device, dtype)
+    dt = torch.float64 if dtype is None else dtype
+    dev = torch.device(device)
+    theta = geom.angles
+    a, b, w = geometry_vectors(theta, geom.tilt)
+    M = params["M"]
+    c = params["centre"]
+    rho = params["rho"]
+    R = 1.0 / np.linalg.svd(M, compute_uv=False)[:, -1]        # largest semi-axis
+    order = np.argsort(R)
+    out = torch.zeros((geom.nproj, geom.det_h, geom.det_w), dtype=dt, device=dev)
+    T = lambda z: torch.as_tensor(np.ascontiguousarray(z), dtype=dt, device=dev)
+    for k0 in range(0, geom.nproj, angle_chunk):
+        k1 = min(geom.nproj, k0 + angle_chunk)
+        A_, B_, W_ = a[k0:k1], b[k0:k1], w[k0:k1]
+        kk = torch.arange(k0, k1, device=dev)
+        for e0 in range(0, len(order), batch):
+            idx = order[e0:e0 + batch]
+            Mb, cb, rb = M[idx], c[idx], rho[idx]
+            h = int(np.ceil(R[idx].max())) + 2
+            off = torch.arange(-h, h + 1, device=dev)
+            Ma = np.einsum("eij,kj->eki", Mb, A_)       # [E, K, 3]
+            Mv = np.einsum("eij,kj->eki", Mb, B_)
+            Mw = np.einsum("eij,kj->eki", Mb, W_)
+            Mc = np.einsum("eij,ej->ei", Mb, cb)[:, None, :]
+            al = (Mw * Mw).sum(-1)
+            bu, bv, b0 = (Mw * Ma).sum(-1), (Mw * Mv).sum(-1), -(Mw * Mc).sum(-1)
+            guu, gvv, guv = (Ma * Ma).sum(-1), (Mv * Mv).sum(-1), (Ma * Mv).sum(-1)
+            gu0, gv0 = -(Ma * Mc).sum(-1), -(Mv * Mc).sum(-1)
+            g00 = (Mc * Mc).sum(-1)[:, :1] - 1.0
+            uc = cb @ A_.T                               # [E, K] projected centres
+            vc = cb @ B_.T
+            j0 = torch.as_tensor(np.rint(uc + geom.det_w / 2.0), dtype=torch.long, device=dev)
+            r0 = torch.as_tensor(np.rint(vc + geom.det_h / 2.0), dtype=torch.long, device=dev)
+            jj = j0[:, :, None, None] + off[None, None, None, :]     # [E, K, 1, P]
+            rr = r0[:, :, None, None] + off[None, None, :, None]     # [E, K, P, 1]
+            U = (jj - geom.det_w / 2.0).to(dt)
+            V = (rr - geom.det_h / 2.0).to(dt)
+            X = lambda z: T(z)[:, :, None, None]
+            beta = X(bu) * U + X(bv) * V + X(b0)
+            gamma = (X(guu) * U * U + 2.0 * X(guv) * U * V + X(gvv) * V * V
+                     + 2.0 * X(gu0) * U + 2.0 * X(gv0) * V + T(g00)[:, :, None, None])
+            disc = beta * beta - X(al) * gamma
+            val = (2.0 * T(rb)[:, None, None, None]) * torch.sqrt(torch.clamp(disc, min=0.0)) / X(al)
+            jjb, rrb = torch.broadcast_tensors(jj, rr)
+            kb = kk[None, :, None, None].expand_as(jjb)
+            ok = (jjb >= 0) & (jjb < geom.det_w) & (rrb >= 0) & (rrb < geom.det_h) & (val > 0)
+            out.index_put_((kb[ok], rrb[ok], jjb[ok]), val[ok], accumulate=True)
+    return out
+
+
 def add_noise(d, frac: float, seed: int):
     """Additive Gaussian noise with sigma = frac * max|d| (seeded, numpy PCG64)."""
     if frac <= 0:
@@ -221,39 +283,54 @@ def add_noise(d, frac: float, seed: int):
     return d + scale * torch.as_tensor(n, device=d.device).to(d.dtype)
 
 
-def add_poisson(d, photons: float, seed: int, mu_scale: float | None = None):
+def add_poisson(d, photons: float, seed: int, mu_scale: float | None = None, chunk: int = 64):
     """Poisson counting noise at `photons` per pixel, returned as line integrals.
 
     The line integrals are scaled so the darkest pixel transmits about 5%, the
-    counts are drawn from I0*exp(-d) and d is re-estimated as -log(counts/I0)
+    counts are drawn from I0*exp(-d) (torch generator on d's device, seeded,
+    chunks of `chunk` projections) and d is re-estimated as -log(counts/I0)
     (a count of 0 is clamped to 0.5). Returns (noisy line integrals, scale).
     """
-    g = torch.Generator(device="cpu").manual_seed(seed + 7919)
+    g = torch.Generator(device=d.device).manual_seed(seed + 7919)
     if mu_scale is None:
         dmax = float(d.max())
         mu_scale = 3.0 / dmax if dmax > 0 else 1.0
-    lam = photons * torch.exp(-(d * mu_scale)).cpu().double()
-    counts = torch.poisson(lam, generator=g).clamp_(min=0.5)
-    return (-torch.log(counts / photons) / mu_scale).to(d.device, d.dtype), mu_scale
+    out = torch.empty_like(d)
+    for k0 in range(0, d.shape[0], chunk):
+        lam = photons * torch.exp(-(d[k0:k0 + chunk].double() * mu_scale))
+        counts = torch.poisson(lam, generator=g).clamp_(min=0.5)
+        out[k0:k0 + chunk] = (-torch.log(counts / photons) / mu_scale).to(d.dtype)
+    return out, mu_scale
 
 
 def make_projections(name: str, device: str = "cpu", dtype=None):
     """Build the seeded synthetic projections of one named workload.
 
-    Returns (geom, params, d) where d is a float32 tensor on `device`.
+    Returns (geom, params, d) where d is a float32 tensor on `device` (use
+    `storage_dtype(name)` for the type the workload stores projections in).
     """
     cfg = CONFIGS[name]
     geom = cfg["geom"]
     if cfg["phantom"] == "blobs":
         params = blob_params(geom, cfg["count"], cfg["seed"], cfg["sigma"], cfg["amp"])
     else:
-        params = ellipsoid_params(geom, cfg["count"], cfg["seed"], cfg.get("dense_frac", 0.0))
-    d = project(params, geom, device=device, dtype=dtype)
+        params = ellipsoid_params(geom, cfg["count"], cfg["seed"], cfg.get("dense_frac", 0.0),
+                                  cfg.get("max_axis"))
+    if params["kind"] == "ellipsoids":
+        d = project_boxed(params, geom, device=device, dtype=dtype)
+    else:
+        d = project(params, geom, device=device, dtype=dtype)
     if "poisson" in cfg:
         d, _ = add_poisson(d, cfg["poisson"], cfg["seed"])
     else:
         d = add_noise(d, cfg["noise"], cfg["seed"])
     return geom, params, d.float()
+
+
+def storage_dtype(name: str):
+    """torch dtype a workload stores its projections in (float32 unless stated)."""
+    st = CONFIGS[name].get("storage", "f32")
+    return {"f32": torch.float32, "f16": torch.float16, "bf16": torch.bfloat16}[st]
 
 
 def rasterize_blobs(params: dict, geom: Geometry) -> np.ndarray:

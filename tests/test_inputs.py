@@ -9,6 +9,7 @@ import math
 
 import numpy as np
 import pytest
+import torch
 
 from paper_2401_11101_gb300 import inputs as I
 
@@ -115,6 +116,23 @@ def test_ellipsoid_projection_total_mass():
     mass = 0.7 * 4.0 / 3.0 * np.pi * axes.prod()
     # midpoint sums of the sqrt-edged chord function converge like h^{3/2}
     assert np.abs(d.sum(axis=(1, 2)) / mass - 1).max() < 2e-3
+
+
+def test_boxed_projection_equals_dense():
+    geom = I.Geometry(48, 40, 24, 9, 30, 70, math.radians(25.0))
+    p = I.ellipsoid_params(geom, 7, seed=9, dense_frac=0.3)
+    a = I.project(p, geom).numpy()
+    b = I.project_boxed(p, geom, angle_chunk=4, batch=3).numpy()
+    assert np.abs(a - b).max() <= 1e-12 * max(1.0, np.abs(a).max())
+
+
+def test_poisson_noise_is_seeded_and_unbiased():
+    geom = I.Geometry(16, 16, 8, 4, 8, 16, 0.3)
+    d = torch.full((4, 8, 16), 0.5, dtype=torch.float64)
+    n1, s1 = I.add_poisson(d, 1e4, 3, mu_scale=1.0)
+    n2, _ = I.add_poisson(d, 1e4, 3, mu_scale=1.0)
+    assert torch.equal(n1, n2)
+    assert abs(float(n1.mean()) - 0.5) < 0.01
 
 
 def test_seeded_inputs_are_reproducible():

@@ -236,6 +236,21 @@ def test_fourier_columns_match_full_volume():
         assert np.abs(dcol[c] - dfull[:, i1, i0]).max() < 1e-15
 
 
+def test_angle_subset_is_the_zeroed_full_sum():
+    # backprojection is a sum over angles: a subset of projections gives the
+    # same result as the full set with the other projections zeroed
+    geom = I.Geometry(12, 10, 6, 9, 8, 20, math.radians(25.0))
+    q = I.random_projections(geom, 16)
+    idx = np.array([1, 4, 8])
+    qz = np.zeros_like(q)
+    qz[idx] = q[idx]
+    cols = np.array([[0, 0], [5, 7], [11, 9]], dtype=np.int32)
+    for fn in (O.backproject_direct_columns, O.backproject_fourier_columns):
+        full = fn(qz, geom, cols)
+        sub = fn(q[idx], geom, cols, angle_index=idx)
+        assert np.abs(full - sub).max() <= 1e-12 * np.abs(full).max()
+
+
 # ---------------------------------------------------------------- P7 scale
 
 def _blob_case(tilt_deg):
