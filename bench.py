@@ -62,6 +62,9 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--cpu-columns", type=int, default=32)
+    ap.add_argument("--no-serve", action="store_true")
+    ap.add_argument("--serve-requests", type=int, default=32)
+    ap.add_argument("--serve-rate", type=float, default=20.0)
     return ap.parse_args()
 
 
@@ -192,6 +195,33 @@ def oracle_fourier_sample(d_cpu: np.ndarray, g, ncols: int, seed: int = 7):
     O.backproject_fourier_columns(q, g, cols)
     dt = time.perf_counter() - t0
     return dt, ncols * g.n2, O.num_threads()
+
+
+# --------------------------------------------------------------------- serving
+
+def run_serving(n: int, rate: float, device: int, seed: int = 5) -> dict:
+    """Mixed stream of FBP requests (Poisson arrivals): volumes from {128^3,
+    256^2x128, 512^2x256, 1024^2x256}, 180-1800 angles, tilt U[10,40] deg,
+    detector width 1.5 x volume width, FP16 ellipsoid-phantom projections
+    (40 ellipsoids per request). Returns the latency / throughput summary."""
+    from paper_2401_11101_gb300 import serve as S
+    reqs = S.mixed_requests(n, rate, seed)
+    t0 = time.perf_counter()
+    for r in reqs:
+        g = I.Geometry(r.n0, r.n1, r.n2, r.nproj, r.det_h, r.det_w, r.tilt)
+        prm = I.ellipsoid_params(g, 40, seed=1000 + r.rid, max_axis=max(4.0, r.n2 / 8.0))
+        d = I.project_boxed(prm, g, device=f"cuda:{device}", dtype=torch.float32)
+        r.d = d.half().cpu().pin_memory()
+        r.form = "fourier"
+    gen_s = time.perf_counter() - t0
+    backend = S.CudaBackend(device, slots=4, keep_volumes=True)
+    # plans and workspaces of every geometry class stay resident across requests
+    rep = S.Server(backend, slots=4).run(reqs)
+    out = rep.summary(reqs)
+    out.update({"rate_req_s": rate, "slots": 4, "form": "fourier", "input_generation_s": gen_s,
+                "workload": "mixed volumes {128^3, 256^2x128, 512^2x256, 1024^2x256}, "
+                            "180-1800 angles, tilt U[10,40] deg, det 1.5 n0 x n2, FP16"})
+    return out
 
 
 # --------------------------------------------------------------------- arms
@@ -346,6 +376,10 @@ def run_ours(args, geom, d):
                "d2h_bytes_per_step": int(v_host.numel() * v_host.element_size()),
                "ms_per_step": te}
 
+    serve = None
+    if not args.no_serve:
+        serve = run_serving(args.serve_requests, args.serve_rate, local)
+
     cpu = None
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:
         dt, vox, thr = oracle_fourier_sample(d.cpu().numpy(), geom, args.cpu_columns)
@@ -369,7 +403,7 @@ def run_ours(args, geom, d):
                           "fourier_over_direct": t_d / t_f},
                 "roofline": roof(dominant), "roofline_fourier": roof(dom_f),
                 "kernels": kernels, "gpu_launches": len(recs),
-                "clocks": clk, "e2e": e2e, "cpu_baseline": cpu}
+                "clocks": clk, "e2e": e2e, "cpu_baseline": cpu, "serve": serve}
         print(json.dumps(line), flush=True)
     plan.close()
 
