@@ -77,6 +77,22 @@ def dist_env():
     return ws, rank, local
 
 
+def max_over_ranks(vals, device):
+    """Element-wise maximum over ranks of per-rank timings: the slowest rank
+    sets the job's time (identity on one process)."""
+    if not (torch.distributed.is_available() and torch.distributed.is_initialized()) \
+            or torch.distributed.get_world_size() == 1:
+        return [float(v) for v in vals]
+    t = torch.tensor([float(v) for v in vals], dtype=torch.float64, device=device)
+    torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+    return t.tolist()
+
+
+def job_gvox_s(nvox_per_rank: int, world: int, ms: float) -> float:
+    """Whole-job throughput: the voxels all ranks reconstructed over the job time."""
+    return world * nvox_per_rank / (ms * 1e-3) / 1e9
+
+
 def measured_peaks():
     path = os.path.join(ROOT, "MEASURED_PEAKS.json")
     if os.path.exists(path):
@@ -306,13 +322,10 @@ def run_ours(args, geom, d):
 
     t_f = sum(e[0].elapsed_time(e[1]) for e in evs) / args.steps
     t_d = sum(e[1].elapsed_time(e[2]) for e in evs) / args.steps
-    if ws > 1:
-        tt = torch.tensor([t_f, t_d], device=dev)
-        torch.distributed.all_reduce(tt, op=torch.distributed.ReduceOp.MAX)
-        t_f, t_d = tt.tolist()
+    t_f, t_d = max_over_ranks([t_f, t_d], dev)
     nvox = geom.nvox
-    value = ws * nvox / (t_f * 1e-3) / 1e9
-    value_d = ws * nvox / (t_d * 1e-3) / 1e9
+    value = job_gvox_s(nvox, ws, t_f)
+    value_d = job_gvox_s(nvox, ws, t_d)
 
     # per-kernel live timing and roofline
     per = {}
@@ -366,12 +379,8 @@ def run_ours(args, geom, d):
             b.record(stream)
             b.synchronize()
             ts.append(a.elapsed_time(b))
-        te = sum(ts) / len(ts)
-        if ws > 1:
-            tt = torch.tensor([te], device=dev)
-            torch.distributed.all_reduce(tt, op=torch.distributed.ReduceOp.MAX)
-            te = tt.item()
-        e2e = {"value": ws * nvox / (te * 1e-3) / 1e9, "unit": "GVox/s",
+        te, = max_over_ranks([sum(ts) / len(ts)], dev)
+        e2e = {"value": job_gvox_s(nvox, ws, te), "unit": "GVox/s",
                "h2d_bytes_per_step": int(d_host.numel() * d_host.element_size()),
                "d2h_bytes_per_step": int(v_host.numel() * v_host.element_size()),
                "ms_per_step": te}
@@ -421,7 +430,8 @@ def main():
             run_reference(args, geom, d)
     else:
         torch.cuda.set_device(local)
-        geom, _, d = I.make_projections(args.workload, device=f"cuda:{local}")
+        # every replica reconstructs its own specimen (seed offset by rank)
+        geom, _, d = I.make_projections(args.workload, device=f"cuda:{local}", slab=rank)
         d = d.to(I.storage_dtype(args.workload)).contiguous()
         run_ours(args, geom, d)
     if ws > 1:

@@ -216,6 +216,19 @@ int lamino_project(lamino_plan_t plan, int form, const float* vol, float* d,
 int lamino_status(lamino_plan_t plan, cudaStream_t stream);
 
 /*
+ * lamino_selftest_wait -- exercise the failure path of bounded device waits
+ * (the method has no counterpart; it is a test hook). Launches on `stream` one
+ * kernel that waits, with the same bounded mbarrier wait as the hot-path
+ * kernels, on a barrier that nothing arrives at. After `limit_us`
+ * microseconds (1 .. 5,000,000, else LAMINO_EINVAL) the wait gives up, the
+ * kernel records the failure in the plan's error word and returns; the next
+ * lamino_status on `stream` then returns LAMINO_ETIMEOUT and clears it. The
+ * device context stays usable. Returns LAMINO_OK once the kernel is queued
+ * (ECUDA if the launch failed).
+ */
+int lamino_selftest_wait(lamino_plan_t plan, unsigned int limit_us, cudaStream_t stream);
+
+/*
  * Tracing: with profiling enabled, every kernel a plan launches is bracketed
  * by two CUDA events recorded on the call's stream. lamino_profile_read waits
  * for the recorded events, returns (name, milliseconds) per launch in launch

@@ -303,13 +303,16 @@ def add_poisson(d, photons: float, seed: int, mu_scale: float | None = None, chu
     return out, mu_scale
 
 
-def make_projections(name: str, device: str = "cpu", dtype=None):
+def make_projections(name: str, device: str = "cpu", dtype=None, slab: int = 0):
     """Build the seeded synthetic projections of one named workload.
 
     Returns (geom, params, d) where d is a float32 tensor on `device` (use
     `storage_dtype(name)` for the type the workload stores projections in).
+    `slab` > 0 draws another independent specimen of the same workload (the
+    seed is offset), as each replica of a multi-GPU run reconstructs its own.
     """
-    cfg = CONFIGS[name]
+    cfg = dict(CONFIGS[name])
+    cfg["seed"] = cfg["seed"] + 1009 * slab
     geom = cfg["geom"]
     if cfg["phantom"] == "blobs":
         params = blob_params(geom, cfg["count"], cfg["seed"], cfg["sigma"], cfg["amp"])

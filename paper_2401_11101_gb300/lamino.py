@@ -30,7 +30,7 @@ FORMS = {"direct": DIRECT, "fourier": FOURIER}
 # every symbol include/lamino.h declares
 EXPORTS = ("lamino_plan", "lamino_get_info", "lamino_filter", "lamino_backproject_direct",
            "lamino_backproject_fourier", "lamino_backproject_fourier_noalloc", "lamino_fbp", "lamino_fbp_host", "lamino_project",
-           "lamino_status", "lamino_profile", "lamino_profile_read", "lamino_workspace_bytes",
+           "lamino_status", "lamino_selftest_wait", "lamino_profile", "lamino_profile_read", "lamino_workspace_bytes",
            "lamino_last_error", "lamino_destroy")
 
 
@@ -79,6 +79,7 @@ def load_library(path: str = LIB_PATH):
     lib.lamino_fbp_host.argtypes = [vp, ci, vp, ci, vp, ci, vp]
     lib.lamino_project.argtypes = [vp, ci, vp, vp, vp]
     lib.lamino_status.argtypes = [vp, vp]
+    lib.lamino_selftest_wait.argtypes = [vp, ctypes.c_uint, vp]
     lib.lamino_workspace_bytes.argtypes = [vp, ci, ctypes.POINTER(sz)]
     lib.lamino_profile.argtypes = [vp, ci]
     lib.lamino_profile_read.argtypes = [vp, ctypes.POINTER(_KTime), ci, ctypes.POINTER(ci)]
@@ -227,6 +228,12 @@ class Plan:
     def status(self):
         """Synchronise the current stream; raise if a bounded device wait expired."""
         self._check(self._lib.lamino_status(self._h, _stream(self.device)))
+
+    def selftest_wait(self, limit_us: int):
+        """Queue a kernel whose bounded wait on a barrier nothing arrives at
+        gives up after limit_us; the next status() raises LaminoError
+        (LAMINO_ETIMEOUT)."""
+        self._check(self._lib.lamino_selftest_wait(self._h, int(limit_us), _stream(self.device)))
 
     def close(self):
         if getattr(self, "_h", None) and self._h.value:
