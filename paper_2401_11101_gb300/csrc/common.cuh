@@ -136,6 +136,7 @@ int launch_direct(lamino_plan_t p, const float* q, float* vol, cudaStream_t s);
 int launch_project_direct(lamino_plan_t p, const float* vol, float* d, cudaStream_t s);
 int launch_project_fourier(lamino_plan_t p, const float* vol, float* d, cudaStream_t s);
 int fourier_workspace(lamino_plan_t p, size_t* a_bytes, size_t* b_bytes);
+int colfft_chunk(lamino_plan_t p);   // columns per column-FFT block = statistics chunk
 
 // device helpers --------------------------------------------------------------
 __device__ __forceinline__ float2 cmul(float2 a, float2 b) {

@@ -29,6 +29,7 @@ namespace {
 // ---------------------------------------------------------------- colfft
 template <int E>
 __global__ void __launch_bounds__(512, 2) k_colfft(const float2* __restrict__ R, float2* __restrict__ G,
+                                                 float2* __restrict__ st,
                                                  int nproj, int H, int Wf, int L, int offv, FftDesc fh,
                                                  const float2* __restrict__ phv, int C) {
     extern __shared__ float2 sm[];
@@ -55,19 +56,38 @@ __global__ void __launch_bounds__(512, 2) k_colfft(const float2* __restrict__ R,
     }
     __syncthreads();
     fft_many<E>(sm, ld, C, fh, -1.f);
+    // write the half spectrum; keep it in shared memory for the statistics
     for (int idx = threadIdx.x; idx < C * L; idx += blockDim.x) {
-        int c = idx % C, l = idx / C;
-        G[((size_t)l * nproj + k) * Wf + m0 + c] = cmul(sm[c * ld + l], __ldg(phv + l));
+        const int c = idx % C, l = idx / C;
+        const float2 g = cmul(sm[c * ld + l], __ldg(phv + l));
+        G[((size_t)l * nproj + k) * Wf + m0 + c] = g;
+        sm[c * ld + l] = g;
+    }
+    __syncthreads();
+    // per plane, the sum and the maximum of max(|Re|, |Im|) over the block's C
+    // columns: the gridding kernel's bound on its fixed-point range.
+    // Layout st[k][m0 / C][l].
+    for (int l = threadIdx.x; l < L; l += blockDim.x) {
+        float sum = 0.f, mx = 0.f;
+        for (int c = 0; c < C; ++c) {
+            const float2 g = sm[c * ld + l];
+            const float av = fmaxf(fabsf(g.x), fabsf(g.y));
+            sum += av;
+            mx = fmaxf(mx, av);
+        }
+        st[((size_t)k * (Wf / C) + m0 / C) * L + l] = make_float2(sum, mx);
     }
 }
 
 // ---------------------------------------------------------------- grid
 struct GridArgs {
     const float2* G;
+    const float2* st;      // [nproj][Wf / ch][L] (sum, max) of max(|Re|, |Im|) per chunk of ch columns
     float2* V;
     const float2* trig;
     const float* dec1;
     int nproj, Wf, Hf, n0, M1, M2, T2, ld;   // ld: row pitch of the band accumulator
+    int ch;                                  // column chunk of the statistics
     float sinphi, c1, c2;  // c = -1/(4t) per axis
     FftDesc f1;
 };
@@ -189,10 +209,14 @@ constexpr int kRoundMagicBits = 0x4B400000;  // its bit pattern
 // [nproj] scratch. Whole block; returns the number of points.
 __device__ __forceinline__ int band_list(const float2* __restrict__ trig, int nproj, int Wf, int M2,
                                          float rho, float lo, float hi, int* ioff, int* ikm,
-                                         int* lcnt, int* scan_tmp, int& nintv_out) {
+                                         int* lcnt, int* scan_tmp, int& nintv_out,
+                                         const float2* __restrict__ st = nullptr, int ch = 1,
+                                         int sstride = 0, float* bsum = nullptr,
+                                         float* bmax = nullptr) {
     const int half = Wf / 2;
     const int per = (nproj + blockDim.x - 1) / blockDim.x;   // lines per thread (<= 4)
     int ms[4][4], me[4][4], nint[4];
+    float ssum = 0.f, smax = 0.f;
 #pragma unroll
     for (int t = 0; t < 4; ++t) {
         nint[t] = 0;
@@ -202,8 +226,20 @@ __device__ __forceinline__ int band_list(const float2* __restrict__ trig, int np
             const float AY = (float)M2 * cs.y / (float)Wf, BY = -(float)M2 * rho * cs.x;
             nint[t] = band_intervals(AY, BY, -half + 1, half - 1, lo, hi, M2, ms[t], me[t]);
             lcnt[k] = nint[t];
+            if (st) {
+                // every chunk that holds a point of the line's intervals: an
+                // upper bound on the band's sum and maximum
+                const float2* sl = st + (size_t)k * (Wf / ch) * sstride;
+                for (int i = 0; i < nint[t]; ++i)
+                    for (int c = (ms[t][i] + half) / ch; c <= (me[t][i] + half) / ch; ++c) {
+                        const float2 v = __ldg(sl + (size_t)c * sstride);
+                        ssum += v.x;
+                        smax = fmaxf(smax, v.y);
+                    }
+            }
         }
     }
+    if (bsum) { *bsum = ssum; *bmax = smax; }
     __syncthreads();
     const int nintv = block_scan(lcnt, nproj, scan_tmp);
 #pragma unroll
@@ -296,25 +332,18 @@ __global__ void __launch_bounds__(768, 1) k_grid(GridArgs a) {
     const float rho = (float)l * a.sinphi / (float)a.Hf;   // k_v sin(phi)
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
     const int half = a.Wf / 2;
-    // points whose 2W rows reach the band: Y in [s20 - W, s20 + T2 + W - 1)
+    // points whose 2W rows reach the band: Y in [s20 - W, s20 + T2 + W - 1);
+    // the chunk statistics of the column pass bound the band's values
     int nintv = 0;
+    float lsum = 0.f, lmax = 0.f;
     const int total = band_list(a.trig, nproj, a.Wf, M2, rho, (float)(s20 - W),
-                                (float)(s20 + T2 + W - 1), ioff, ikm, lcnt, scan_tmp, nintv);
+                                (float)(s20 + T2 + W - 1), ioff, ikm, lcnt, scan_tmp, nintv,
+                                a.st + l, a.ch, gridDim.y, &lsum, &lmax);
     auto locate = [&](int base, int& k, int& m) -> bool {
         return band_locate(ioff, ikm, nintv, total, base, lane, k, m);
     };
 
     const float2* Gl = a.G + (size_t)l * nproj * a.Wf;
-    // pass 1: bound the band
-    float lsum = 0.f, lmax = 0.f;
-    for (int base = warp * 32; base < total; base += nwarps * 32) {
-        int k, m;
-        if (!locate(base, k, m)) continue;
-        const float2 g = Gl[(size_t)k * a.Wf + (m + half)];
-        const float v = fmaxf(fabsf(g.x), fabsf(g.y));
-        lsum += v;
-        lmax = fmaxf(lmax, v);
-    }
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) {
         lsum += __shfl_xor_sync(0xffffffffu, lsum, o);
@@ -324,6 +353,8 @@ __global__ void __launch_bounds__(768, 1) k_grid(GridArgs a) {
     __syncthreads();
     float S1 = 0.f, Smax = 0.f;
     for (int i = 0; i < nwarps; ++i) { S1 += red_s[i]; Smax = fmaxf(Smax, red_m[i]); }
+    // the sums run in float: 1 % headroom covers their rounding
+    S1 *= 1.01f;
     const float q = (S1 > 0.f) ? fminf(1073741824.0f / S1, 2097152.0f / Smax) : 1.0f;
 
     // pass 2: spread
@@ -729,27 +760,37 @@ int dispatch_grid_w(int w, const GridArgs& a, dim3 grid, int threads, size_t sme
 
 }  // namespace
 
+// Columns per block of the column FFT (a power of two dividing Wf, at most
+// 16, with the block's sequences within 100 KB of shared memory); also the
+// chunk of the statistics it writes for the gridding kernel.
+int colfft_chunk(lamino_plan_t p) {
+    int C = largest_pow2_divisor_upto(p->Wf, 16);
+    while (C > 1 && (size_t)C * (p->Hf + 1) * sizeof(float2) > 100 * 1024) C /= 2;
+    return C;
+}
+
 int run_fourier_after_rows(lamino_plan_t p, float* vol, cudaStream_t s) {
     float2* R = (float2*)p->ws_a;   // row spectra   [nproj][H][Wf]
     float2* G = (float2*)p->ws_b;   // half spectra  [L][nproj][Wf]
     float2* V = (float2*)p->ws_a;   // x1 pass       [L][n0][M2]   (R is dead by then)
     float2* P = (float2*)p->ws_b;   // planes        [L][n1][n0]   (G is dead by then)
 
-    // column FFT
+    // column FFT (+ chunk statistics for the gridding bound, after G in B)
+    const int CH = colfft_chunk(p);
+    float2* st = G + (size_t)p->L * p->nproj * p->Wf;
     {
         const FftDesc& f = p->fHf;
-        int C = largest_pow2_divisor_upto(p->Wf, 16);
-        while (C > 1 && (size_t)C * (f.n + 1) * sizeof(float2) > 100 * 1024) C /= 2;
+        const int C = CH;
         size_t smem = (size_t)C * (f.n + 1) * sizeof(float2);
         dim3 grid(p->Wf / C, p->nproj);
         int threads = std::min(512, std::max(C * f.t, 128));
         ProfScope prof(p, "colfft", s);
         if (f.e == 8) {
             set_smem(k_colfft<8>, smem);
-            k_colfft<8><<<grid, threads, smem, s>>>(R, G, p->nproj, p->H, p->Wf, p->L, p->offv, f, p->d_phv, C);
+            k_colfft<8><<<grid, threads, smem, s>>>(R, G, st, p->nproj, p->H, p->Wf, p->L, p->offv, f, p->d_phv, C);
         } else {
             set_smem(k_colfft<12>, smem);
-            k_colfft<12><<<grid, threads, smem, s>>>(R, G, p->nproj, p->H, p->Wf, p->L, p->offv, f, p->d_phv, C);
+            k_colfft<12><<<grid, threads, smem, s>>>(R, G, st, p->nproj, p->H, p->Wf, p->L, p->offv, f, p->d_phv, C);
         }
         LAM_LAUNCH_CHECK(p, "column FFT kernel");
     }
@@ -757,6 +798,7 @@ int run_fourier_after_rows(lamino_plan_t p, float* vol, cudaStream_t s) {
     {
         GridArgs a;
         a.G = G; a.V = V; a.trig = p->d_trig; a.dec1 = p->d_dec1;
+        a.st = st; a.ch = CH;
         a.nproj = p->nproj; a.Wf = p->Wf; a.Hf = p->Hf; a.n0 = p->n0; a.M1 = p->M1; a.M2 = p->M2;
         a.sinphi = (float)sin(p->tilt);
         a.c1 = (float)(-1.0 / (4.0 * p->t1));
@@ -871,6 +913,7 @@ int launch_project_fourier(lamino_plan_t p, const float* vol, float* d, cudaStre
     {   // gridding transpose
         GridArgs a;
         a.G = nullptr; a.V = nullptr; a.trig = p->d_trig; a.dec1 = p->d_dec1;
+        a.st = nullptr; a.ch = 1;
         a.nproj = p->nproj; a.Wf = p->Wf; a.Hf = p->Hf; a.n0 = p->n0; a.M1 = p->M1; a.M2 = p->M2;
         a.sinphi = (float)sin(p->tilt);
         a.c1 = (float)(-1.0 / (4.0 * p->t1));

@@ -354,6 +354,7 @@ int fourier_workspace(lamino_plan_t p, size_t* a_bytes, size_t* b_bytes) {
     size_t R = (size_t)p->nproj * p->H * p->Wf;    // row spectra
     size_t V = (size_t)p->L * p->n0 * p->M2;       // planes after the x1 pass
     size_t G = (size_t)p->L * p->nproj * p->Wf;    // half spectra, plane-major
+    G += G / colfft_chunk(p);                      // + chunk statistics (sum, max)
     size_t P = (size_t)p->L * p->n1 * p->n0;       // deconvolved planes
     *a_bytes = sizeof(float2) * std::max(R, V);
     *b_bytes = sizeof(float2) * std::max(G, P);
