@@ -223,9 +223,23 @@ struct SeqP {
 // outputs are written back in place (the barrier separates all reads from all
 // writes). Butterfly j reads x[j + r n/R]; with k = j mod ns it twiddles by
 // exp(-+2 pi i k r/(ns R)), transforms and writes x[(j - k) R + k + r ns].
+// Barrier of the threads that share one FFT sequence: the whole block
+// (mode 0), the warp (mode 1: groups of at most 32 threads) or named barrier
+// 1 + gid over the group's T threads (mode 2). Every thread of the group
+// reaches every call, active or not.
+__device__ __forceinline__ void fft_sync(int mode, int gid, int T) {
+    if (mode == 0) {
+        __syncthreads();
+    } else if (mode == 1) {
+        __syncwarp();
+    } else {
+        asm volatile("bar.sync %0, %1;" ::"r"(gid + 1), "r"(T) : "memory");
+    }
+}
+
 template <int E, int R, typename S>
 __device__ __forceinline__ void fft_stage(S x, const FftDesc& f, int tid, bool active, int ns,
-                                          float s) {
+                                          float s, int smode = 0, int gid = 0, int gT = 0) {
     static_assert(E % R == 0, "radix must divide the elements per thread");
     float2 v[E];
     const int n = f.n, t = f.t, nr = n / R;
@@ -237,7 +251,7 @@ __device__ __forceinline__ void fft_stage(S x, const FftDesc& f, int tid, bool a
             for (int r = 0; r < R; ++r) v[i * R + r] = x.ld(j + r * nr);
         }
     }
-    __syncthreads();
+    fft_sync(smode, gid, gT);
     if (active) {
         const int stride = n / (ns * R);
 #pragma unroll
@@ -259,7 +273,7 @@ __device__ __forceinline__ void fft_stage(S x, const FftDesc& f, int tid, bool a
             for (int r = 0; r < R; ++r) x.st(d + r * ns, v[i * R + r]);
         }
     }
-    __syncthreads();
+    fft_sync(smode, gid, gT);
 }
 
 // Complex FFT of the length-f.n sequence x (shared memory), exponent sign s.
@@ -267,22 +281,32 @@ __device__ __forceinline__ void fft_stage(S x, const FftDesc& f, int tid, bool a
 // active == false only take part in the barriers. Output is in natural order,
 // unnormalised.
 template <int E, typename S>
-__device__ __forceinline__ void fft_run(S x, const FftDesc& f, int tid, bool active, float s) {
+__device__ __forceinline__ void fft_run(S x, const FftDesc& f, int tid, bool active, float s,
+                                        int smode = 0, int gid = 0, int gT = 0) {
     active = active && tid < f.t;
     int ns = 1;
     for (int st = 0; st < f.nst; ++st) {
         const int R = (f.rads >> (4 * st)) & 15u;
         if constexpr (E % 8 == 0) {
-            if (R == 8) fft_stage<E, 8>(x, f, tid, active, ns, s);
-            else if (R == 4) fft_stage<E, 4>(x, f, tid, active, ns, s);
-            else fft_stage<E, 2>(x, f, tid, active, ns, s);
+            if (R == 8) fft_stage<E, 8>(x, f, tid, active, ns, s, smode, gid, gT);
+            else if (R == 4) fft_stage<E, 4>(x, f, tid, active, ns, s, smode, gid, gT);
+            else fft_stage<E, 2>(x, f, tid, active, ns, s, smode, gid, gT);
         } else {
-            if (R == 4) fft_stage<E, 4>(x, f, tid, active, ns, s);
-            else if (R == 2) fft_stage<E, 2>(x, f, tid, active, ns, s);
-            else fft_stage<E, 3>(x, f, tid, active, ns, s);
+            if (R == 4) fft_stage<E, 4>(x, f, tid, active, ns, s, smode, gid, gT);
+            else if (R == 2) fft_stage<E, 2>(x, f, tid, active, ns, s, smode, gid, gT);
+            else fft_stage<E, 3>(x, f, tid, active, ns, s, smode, gid, gT);
         }
         ns *= R;
     }
+}
+
+// Barrier mode of fft_many: per-group barriers when the block splits into
+// whole groups of T threads (at most 15 named barriers), else the block.
+__device__ __forceinline__ int fft_group_mode(int T) {
+    const int nb = blockDim.x;
+    if (nb % T != 0 || nb % 32 != 0) return 0;
+    if (T <= 32) return 1;
+    return (nb / T <= 15) ? 2 : 0;
 }
 
 template <int E>
@@ -292,29 +316,35 @@ __device__ __forceinline__ void fft_run(float2* x, const FftDesc& f, int tid, bo
 
 // FFTs of nseq sequences at base + i*ld with every thread of the block: groups
 // of blockDim/f.t sequences run side by side (blockDim must be >= f.t).
+// Ends with a block-wide barrier.
 template <int E>
 __device__ __forceinline__ void fft_many(float2* base, int ld, int nseq, const FftDesc& f, float s) {
     const int T = f.t;
     const int par = blockDim.x / T;
     const int g = threadIdx.x / T;
+    const int mode = fft_group_mode(T);
     for (int s0 = 0; s0 < nseq; s0 += par) {
         const int seq = s0 + g;
         fft_run<E>(SeqC{base + (size_t)min(seq, nseq - 1) * ld}, f, threadIdx.x % T,
-                   g < par && seq < nseq, s);
+                   g < par && seq < nseq, s, mode, g, T);
     }
+    if (mode != 0) __syncthreads();
 }
 
 // The same for planar sequences re + i*ld, im + i*ld.
+// Ends with a block-wide barrier.
 template <int E>
 __device__ __forceinline__ void fft_many_planar(float* re, float* im, int ld, int nseq,
                                                 const FftDesc& f, float s) {
     const int T = f.t;
     const int par = blockDim.x / T;
     const int g = threadIdx.x / T;
+    const int mode = fft_group_mode(T);
     for (int s0 = 0; s0 < nseq; s0 += par) {
         const size_t o = (size_t)min(s0 + g, nseq - 1) * ld;
-        fft_run<E>(SeqP{re + o, im + o}, f, threadIdx.x % T, g < par && s0 + g < nseq, s);
+        fft_run<E>(SeqP{re + o, im + o}, f, threadIdx.x % T, g < par && s0 + g < nseq, s, mode, g, T);
     }
+    if (mode != 0) __syncthreads();
 }
 
 }  // namespace lam

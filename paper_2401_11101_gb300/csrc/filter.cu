@@ -126,9 +126,12 @@ __global__ void __launch_bounds__(512, 1) k_rowfft(const Tin* __restrict__ d, fl
     }
 }
 
+// Row pairs per block: blocks of about 128 threads (one pair for rows of
+// 1024 or more): small blocks wait on fewer warps at each FFT barrier and
+// more of them share an SM.
 int pairs_for(int T, size_t bytes_per_pair) {
     int pairs = 1;
-    while (pairs * 2 * T <= 512 && (pairs * 2) * bytes_per_pair <= 64 * 1024) pairs *= 2;
+    while (pairs * 2 * T <= 128 && (pairs * 2) * bytes_per_pair <= 64 * 1024) pairs *= 2;
     return pairs;
 }
 
