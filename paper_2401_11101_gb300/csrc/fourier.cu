@@ -88,6 +88,7 @@ struct GridArgs {
     const float* dec1;
     int nproj, Wf, Hf, n0, M1, M2, T2, ld;   // ld: row pitch of the band accumulator
     int ch;                                  // column chunk of the statistics
+    int civ_cap;                             // entries of the group table (0: none)
     float sinphi, c1, c2;  // c = -1/(4t) per axis
     FftDesc f1;
 };
@@ -212,7 +213,8 @@ __device__ __forceinline__ int band_list(const float2* __restrict__ trig, int np
                                          int* lcnt, int* scan_tmp, int& nintv_out,
                                          const float2* __restrict__ st = nullptr, int ch = 1,
                                          int sstride = 0, float* bsum = nullptr,
-                                         float* bmax = nullptr) {
+                                         float* bmax = nullptr, int* civ = nullptr,
+                                         int civ_cap = 0) {
     const int half = Wf / 2;
     const int per = (nproj + blockDim.x - 1) / blockDim.x;   // lines per thread (<= 4)
     int ms[4][4], me[4][4], nint[4];
@@ -257,25 +259,37 @@ __device__ __forceinline__ int band_list(const float2* __restrict__ trig, int np
     const int total = block_scan(ioff, nintv, scan_tmp);
     if (threadIdx.x == 0) ioff[nintv] = total;
     __syncthreads();
+    if (civ && total <= 32 * civ_cap) {
+        // group table: civ[g] = the interval that holds point 32 g
+        for (int i = threadIdx.x; i < nintv; i += blockDim.x)
+            for (int g = (ioff[i] + 31) >> 5; 32 * g < ioff[i + 1]; ++g) civ[g] = i;
+        __syncthreads();
+    }
     nintv_out = nintv;
     return total;
 }
 
-// Point number base + lane of a band list -> (line k, m); lane 0 finds the
-// interval of `base` by bisection and every lane steps forward from it. Must be
+// Point number base + lane of a band list -> (line k, m); the interval of
+// `base` (a multiple of 32) comes from the group table civ when there is one,
+// else lane 0 finds it by bisection; every lane steps forward from it. Must be
 // called by the whole warp; false for lanes past the end.
 __device__ __forceinline__ bool band_locate(const int* ioff, const int* ikm, int nintv, int total,
-                                            int base, int lane, int& k, int& m) {
+                                            int base, int lane, int& k, int& m,
+                                            const int* civ = nullptr) {
     int iv = 0;
-    if (lane == 0) {
-        int a0 = 0, b0 = nintv;   // ioff[a0] <= base < ioff[b0]
-        while (b0 - a0 > 1) {
-            const int mid = (a0 + b0) >> 1;
-            if (ioff[mid] <= base) a0 = mid; else b0 = mid;
+    if (civ) {
+        iv = civ[base >> 5];
+    } else {
+        if (lane == 0) {
+            int a0 = 0, b0 = nintv;   // ioff[a0] <= base < ioff[b0]
+            while (b0 - a0 > 1) {
+                const int mid = (a0 + b0) >> 1;
+                if (ioff[mid] <= base) a0 = mid; else b0 = mid;
+            }
+            iv = a0;
         }
-        iv = a0;
+        iv = __shfl_sync(0xffffffffu, iv, 0);
     }
-    iv = __shfl_sync(0xffffffffu, iv, 0);
     const int p = base + lane;
     if (p >= total) return false;
     while (ioff[iv + 1] <= p) ++iv;
@@ -310,7 +324,7 @@ struct TapRow<N, N> {
 };
 
 template <int E, int W>
-__global__ void __launch_bounds__(768, 1) k_grid(GridArgs a) {
+__global__ void __launch_bounds__(1024, 1) k_grid(GridArgs a) {
     extern __shared__ float smf[];
     const int M1 = a.M1, M2 = a.M2, T2 = a.T2, ld = a.ld;
     const int nproj = a.nproj;
@@ -321,6 +335,7 @@ __global__ void __launch_bounds__(768, 1) k_grid(GridArgs a) {
     int* ioff = reinterpret_cast<int*>(Uim + (size_t)T2 * ld);
     int* ikm = ioff + 4 * nproj + 1;
     int* lcnt = ikm + 4 * nproj;            // [nproj] per-line interval counts (scan)
+    int* civ = lcnt + nproj;                // [civ_cap] group table of the band list
     __shared__ float red_s[32], red_m[32];
     __shared__ int scan_tmp[32];
     const int band = blockIdx.x, l = blockIdx.y;
@@ -338,9 +353,10 @@ __global__ void __launch_bounds__(768, 1) k_grid(GridArgs a) {
     float lsum = 0.f, lmax = 0.f;
     const int total = band_list(a.trig, nproj, a.Wf, M2, rho, (float)(s20 - W),
                                 (float)(s20 + T2 + W - 1), ioff, ikm, lcnt, scan_tmp, nintv,
-                                a.st + l, a.ch, gridDim.y, &lsum, &lmax);
+                                a.st + l, a.ch, gridDim.y, &lsum, &lmax, civ, a.civ_cap);
+    const int* civ_t = (total <= 32 * a.civ_cap) ? civ : nullptr;
     auto locate = [&](int base, int& k, int& m) -> bool {
-        return band_locate(ioff, ikm, nintv, total, base, lane, k, m);
+        return band_locate(ioff, ikm, nintv, total, base, lane, k, m, civ_t);
     };
 
     const float2* Gl = a.G + (size_t)l * nproj * a.Wf;
@@ -388,12 +404,18 @@ __global__ void __launch_bounds__(768, 1) k_grid(GridArgs a) {
         r0 += (r0 < 0) ? M2 : 0;
         r0 += (r0 < 0) ? M2 : 0;
         r0 -= (r0 >= M2) ? M2 : 0;                      // now in [0, M2); 2W <= M2
+        float gyv[2 * W];
+#pragma unroll
+        for (int jy = 0; jy < 2 * W; ++jy) {
+            const float dy = (float)((int)fy - W + 1 + jy) - Y;
+            gyv[jy] = __expf(a.c2 * dy * dy);
+        }
+#pragma unroll
         for (int jy = 0; jy < 2 * W; ++jy) {
             int rr = r0 + jy;
             rr -= (rr >= M2) ? M2 : 0;
             if ((unsigned)rr >= (unsigned)T2) continue;
-            const float dy = (float)((int)fy - W + 1 + jy) - Y;
-            const float gy = __expf(a.c2 * dy * dy);
+            const float gy = gyv[jy];
             const float vr = g.x * gy, vi = g.y * gy;
             const uint32_t row = s_re + 4u * (uint32_t)(rr * ld);
             if (!wraps) {
@@ -819,7 +841,10 @@ int run_fourier_after_rows(lamino_plan_t p, float* vol, cudaStream_t s) {
         size_t smem = (size_t)T2 * a.ld * sizeof(float2) + sizeof(int) * (9 * (size_t)p->nproj + 1);
         if (smem > 220 * 1024)
             return fail(p, LAMINO_EUNSUPPORTED, "gridding tile of %zu bytes exceeds shared memory", smem);
-        int threads = 768;
+        // group table in what is left (bands with more points bisect instead)
+        a.civ_cap = (int)std::min<size_t>(16384, (224 * 1024 - smem) / sizeof(int));
+        smem += sizeof(int) * (size_t)a.civ_cap;
+        int threads = 1024;
         dim3 grid(p->M2 / T2, p->L);
         ProfScope prof(p, "grid", s);
         if (p->fM1.e == 8) dispatch_grid_w<8>(p->w, a, grid, threads, smem, s);
@@ -913,7 +938,7 @@ int launch_project_fourier(lamino_plan_t p, const float* vol, float* d, cudaStre
     {   // gridding transpose
         GridArgs a;
         a.G = nullptr; a.V = nullptr; a.trig = p->d_trig; a.dec1 = p->d_dec1;
-        a.st = nullptr; a.ch = 1;
+        a.st = nullptr; a.ch = 1; a.civ_cap = 0;
         a.nproj = p->nproj; a.Wf = p->Wf; a.Hf = p->Hf; a.n0 = p->n0; a.M1 = p->M1; a.M2 = p->M2;
         a.sinphi = (float)sin(p->tilt);
         a.c1 = (float)(-1.0 / (4.0 * p->t1));
