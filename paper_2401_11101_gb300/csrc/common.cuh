@@ -209,6 +209,17 @@ struct SeqC {
     __device__ __forceinline__ float2 ld(int i) const { return p[i]; }
     __device__ __forceinline__ void st(int i, float2 v) const { p[i] = v; }
 };
+// Interleaved complex with one empty slot after every 16 elements: the
+// strided accesses of the first radix-8 / radix-4 Stockham stages then spread
+// over all banks instead of 2-4 of them.
+__device__ __forceinline__ int fpad(int i) { return i + (i >> 4); }
+// slots a padded sequence of n elements occupies
+__host__ __device__ constexpr int fpad_len(int n) { return n + ((n - 1) >> 4); }
+struct SeqCP {
+    float2* p;
+    __device__ __forceinline__ float2 ld(int i) const { return p[fpad(i)]; }
+    __device__ __forceinline__ void st(int i, float2 v) const { p[fpad(i)] = v; }
+};
 struct SeqP {
     float* re;
     float* im;
@@ -326,6 +337,21 @@ __device__ __forceinline__ void fft_many(float2* base, int ld, int nseq, const F
     for (int s0 = 0; s0 < nseq; s0 += par) {
         const int seq = s0 + g;
         fft_run<E>(SeqC{base + (size_t)min(seq, nseq - 1) * ld}, f, threadIdx.x % T,
+                   g < par && seq < nseq, s, mode, g, T);
+    }
+    if (mode != 0) __syncthreads();
+}
+
+// The same for padded sequences (SeqCP) at base + i*ld.
+template <int E>
+__device__ __forceinline__ void fft_many_padded(float2* base, int ld, int nseq, const FftDesc& f, float s) {
+    const int T = f.t;
+    const int par = blockDim.x / T;
+    const int g = threadIdx.x / T;
+    const int mode = fft_group_mode(T);
+    for (int s0 = 0; s0 < nseq; s0 += par) {
+        const int seq = s0 + g;
+        fft_run<E>(SeqCP{base + (size_t)min(seq, nseq - 1) * ld}, f, threadIdx.x % T,
                    g < par && seq < nseq, s, mode, g, T);
     }
     if (mode != 0) __syncthreads();

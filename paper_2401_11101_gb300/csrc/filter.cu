@@ -15,7 +15,8 @@ namespace lam {
 namespace {
 
 // Rows rA and rA + 1 (if hasB) into x[j] = (a[j - off], b[j - off]) for j in
-// [0, N), zero outside [off, off + W); 8 independent loads in flight per thread.
+// [0, N), zero outside [off, off + W), x a padded sequence (SeqCP layout);
+// 8 independent loads in flight per thread.
 template <typename Tin>
 __device__ __forceinline__ void load_pair_rows(const Tin* __restrict__ d, float2* x, long rA, bool hasB,
                                                int W, int N, int off, int tid, int T) {
@@ -32,7 +33,7 @@ __device__ __forceinline__ void load_pair_rows(const Tin* __restrict__ d, float2
         }
 #pragma unroll
         for (int u = 0; u < U; ++u)
-            if (base + u * T < N) x[base + u * T] = make_float2(a[u], b[u]);
+            if (base + u * T < N) x[fpad(base + u * T)] = make_float2(a[u], b[u]);
     }
 }
 
@@ -49,20 +50,21 @@ __global__ void __launch_bounds__(512, 1) k_filter(const Tin* __restrict__ d, fl
     const long rA = 2 * pair, rB = 2 * pair + 1;
     const bool active = seq < pairs && rA < nrows;
     const bool hasB = rB < nrows;
-    float2* x = sm + (size_t)seq * N;
+    float2* x = sm + (size_t)seq * fpad_len(N);
     if (active) load_pair_rows(d, x, rA, hasB, W, N, 0, tid, T);
     __syncthreads();
-    fft_run<E>(x, fp, tid, active, -1.f);
+    fft_run<E>(SeqCP{x}, fp, tid, active, -1.f);
     if (active)
         for (int j = tid; j < N; j += T) {
             float h = __ldg(filt + j);
-            x[j] = make_float2(x[j].x * h, x[j].y * h);
+            const float2 v = x[fpad(j)];
+            x[fpad(j)] = make_float2(v.x * h, v.y * h);
         }
     __syncthreads();
-    fft_run<E>(x, fp, tid, active, +1.f);
+    fft_run<E>(SeqCP{x}, fp, tid, active, +1.f);
     if (active)
         for (int j = tid; j < W; j += T) {
-            float2 v = x[j];
+            float2 v = x[fpad(j)];
             q[(size_t)rA * W + j] = v.x;
             if (hasB) q[(size_t)rB * W + j] = v.y;
         }
@@ -85,36 +87,38 @@ __global__ void __launch_bounds__(512, 1) k_rowfft(const Tin* __restrict__ d, fl
     const long rA = 2 * pair, rB = 2 * pair + 1;
     const bool active = seq < pairs && rA < nrows;
     const bool hasB = rB < nrows;
-    float2* xp = sm + (size_t)seq * (Np + Nf);
-    float2* xf = xp + Np;
+    const int Lp = (EP > 0) ? fpad_len(Np) : 0;
+    float2* xp = sm + (size_t)seq * (Lp + fpad_len(Nf));
+    float2* xf = xp + Lp;
     if constexpr (EP > 0) {
         if (active) load_pair_rows(d, xp, rA, hasB, W, Np, 0, tid, T);
         __syncthreads();
-        fft_run<EP>(xp, fp, tid, active, -1.f);
+        fft_run<EP>(SeqCP{xp}, fp, tid, active, -1.f);
         if (active)
             for (int j = tid; j < Np; j += T) {
                 float h = __ldg(filt + j);
-                xp[j] = make_float2(xp[j].x * h, xp[j].y * h);
+                const float2 v = xp[fpad(j)];
+                xp[fpad(j)] = make_float2(v.x * h, v.y * h);
             }
         __syncthreads();
-        fft_run<EP>(xp, fp, tid, active, +1.f);
+        fft_run<EP>(SeqCP{xp}, fp, tid, active, +1.f);
         if (active)
             for (int j = tid; j < Nf; j += T) {
                 int src = j - offu;
-                xf[j] = (src >= 0 && src < W) ? xp[src] : make_float2(0.f, 0.f);
+                xf[fpad(j)] = (src >= 0 && src < W) ? xp[fpad(src)] : make_float2(0.f, 0.f);
             }
     } else {
         if (active) load_pair_rows(d, xf, rA, hasB, W, Nf, offu, tid, T);
     }
     __syncthreads();
-    fft_run<EF>(xf, ff, tid, active, -1.f);
+    fft_run<EF>(SeqCP{xf}, ff, tid, active, -1.f);
     if (active) {
         const int half = Nf / 2;
         for (int mi = tid; mi < Nf; mi += T) {
             int m = mi - half;
             int i1 = m < 0 ? m + Nf : m;          // index of +m
             int i2 = m > 0 ? Nf - m : -m;         // index of -m
-            float2 Z = xf[i1], Zc = xf[i2];
+            float2 Z = xf[fpad(i1)], Zc = xf[fpad(i2)];
             Zc.y = -Zc.y;
             float2 A = make_float2(0.5f * (Z.x + Zc.x), 0.5f * (Z.y + Zc.y));
             float2 Dm = csub(Z, Zc);
@@ -140,8 +144,8 @@ int filter_typed(lamino_plan_t p, const Tin* d, float* q, int kind, cudaStream_t
     const FftDesc& f = p->fWp;
     long nrows = (long)p->nproj * p->H;
     long npairs = (nrows + 1) / 2;
-    int pairs = pairs_for(f.t, sizeof(float2) * f.n);
-    size_t smem = sizeof(float2) * f.n * pairs;
+    int pairs = pairs_for(f.t, sizeof(float2) * fpad_len(f.n));
+    size_t smem = sizeof(float2) * fpad_len(f.n) * pairs;
     dim3 grid((unsigned)((npairs + pairs - 1) / pairs));
     const float* filt = p->d_filt + (size_t)kind * p->Wp;
     ProfScope prof(p, "filter", s);
@@ -160,7 +164,7 @@ template <int EP, int EF, typename Tin>
 int rowfft_launch(lamino_plan_t p, const Tin* d, float2* R, const float* filt, cudaStream_t s) {
     const int Tp = (EP > 0) ? p->fWp.t : 0;
     const int T = std::max(Tp, p->fWf.t);
-    const size_t per_pair = sizeof(float2) * ((EP > 0 ? p->Wp : 0) + p->Wf);
+    const size_t per_pair = sizeof(float2) * ((EP > 0 ? fpad_len(p->Wp) : 0) + fpad_len(p->Wf));
     int pairs = pairs_for(T, per_pair);
     long nrows = (long)p->nproj * p->H;
     long npairs = (nrows + 1) / 2;
