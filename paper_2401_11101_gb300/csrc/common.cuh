@@ -342,21 +342,6 @@ __device__ __forceinline__ void fft_many(float2* base, int ld, int nseq, const F
     if (mode != 0) __syncthreads();
 }
 
-// The same for padded sequences (SeqCP) at base + i*ld.
-template <int E>
-__device__ __forceinline__ void fft_many_padded(float2* base, int ld, int nseq, const FftDesc& f, float s) {
-    const int T = f.t;
-    const int par = blockDim.x / T;
-    const int g = threadIdx.x / T;
-    const int mode = fft_group_mode(T);
-    for (int s0 = 0; s0 < nseq; s0 += par) {
-        const int seq = s0 + g;
-        fft_run<E>(SeqCP{base + (size_t)min(seq, nseq - 1) * ld}, f, threadIdx.x % T,
-                   g < par && seq < nseq, s, mode, g, T);
-    }
-    if (mode != 0) __syncthreads();
-}
-
 // The same for planar sequences re + i*ld, im + i*ld.
 // Ends with a block-wide barrier.
 template <int E>
