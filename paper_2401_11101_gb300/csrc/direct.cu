@@ -121,7 +121,10 @@ __global__ void __launch_bounds__(kThreads) k_direct(const __grid_constant__ CUt
     }
 
     // ---------------- consumers ----------------
-    const int tx = threadIdx.x % TX, ty = threadIdx.x / TX, lane = threadIdx.x & 31;
+    // a warp covers an 8 x 4 patch of columns: its lanes then sample at most
+    // ~5 detector rows instead of up to 11
+    const int lane = threadIdx.x & 31, wq = threadIdx.x >> 5;
+    const int tx = (lane & 7) + 8 * (wq & 3), ty = (lane >> 3) + 4 * (wq >> 2);
     float acc[TZ];
 #pragma unroll
     for (int z = 0; z < TZ; ++z) acc[z] = 0.f;
@@ -147,10 +150,10 @@ __global__ void __launch_bounds__(kThreads) k_direct(const __grid_constant__ CUt
         // the walk adds at most TZ rows; the stage buffers carry TZ + 2 rows of
         // slack after the last stage, so every read stays inside shared memory
         r0 = min(max(r0, 0), bh - 2);
-        const float* col = tile + j0;
-        const float* p = col + r0 * bw;
+        const float* p = tile + j0 + r0 * bw;
         float h_lo = fmaf(fj, p[1] - p[0], p[0]);              // row r0, lerped in u
-        float h_hi = fmaf(fj, p[bw + 1] - p[bw], p[bw]);       // row r0 + 1
+        p += bw;                                               // row r0 + 1
+        float h_hi = fmaf(fj, p[1] - p[0], p[0]);
 #pragma unroll
         for (int z = 0; z < TZ; ++z) {
             acc[z] += fmaf(fr, h_hi - h_lo, h_lo);
@@ -159,7 +162,7 @@ __global__ void __launch_bounds__(kThreads) k_direct(const __grid_constant__ CUt
             fr = adv ? fr - 1.f : fr;
             p += adv ? bw : 0;
             h_lo = adv ? h_hi : h_lo;
-            h_hi = fmaf(fj, p[bw + 1] - p[bw], p[bw]);
+            h_hi = fmaf(fj, p[1] - p[0], p[0]);
         }
         __syncwarp();
         if (lane == 0) mbar_arrive(smem_addr(empty + s));
