@@ -191,7 +191,12 @@ int lamino_fbp(lamino_plan_t plan, int form, const void* d, int dtype, float* vo
 /*
  * lamino_fbp_host -- lamino_fbp on HOST buffers: copies d (host, pinned or
  * pageable) to a plan-owned device buffer, reconstructs, and copies the
- * volume back to vol (host). Synchronises `stream` before returning.
+ * volume back to vol (host). The copies run on a plan-owned stream in chunks
+ * (up to 8 of whole projections up, up to 8 slabs of x2 rows of the Fourier
+ * volume down) so that they overlap the row / column passes and the x3 pass
+ * on `stream`; with pinned host memory the transfers hide behind the
+ * kernels. The result equals lamino_fbp's. Synchronises `stream` (and the
+ * copy stream) before returning; errors as lamino_fbp.
  */
 int lamino_fbp_host(lamino_plan_t plan, int form, const void* d_host, int dtype,
                     float* vol_host, int kind, cudaStream_t stream);

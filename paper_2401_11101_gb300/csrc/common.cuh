@@ -77,6 +77,8 @@ struct lamino_plan_s {
     float* q_buf = nullptr; size_t q_buf_bytes = 0; // filtered rows (direct FBP)
     void* h_in = nullptr; size_t h_in_bytes = 0;   // device copy of host input
     float* h_vol = nullptr; size_t h_vol_bytes = 0;
+    cudaStream_t copy_stream = nullptr;            // host pipeline: copies overlap kernels
+    std::vector<cudaEvent_t> pipe_ev;              // host pipeline: chunk events
 
     lam::DirectCfg dcfg;
     bool filter_ok = false;        // Wp is a supported FFT length
@@ -126,11 +128,21 @@ struct ProfScope {
 };
 
 // kernels' host launchers (defined in the .cu files) ---------------------------
+// Row kernels take the detector rows [row0, row1) (row = k H + r; row1 < 0:
+// all rows), so that a host pipeline can start on the projections already copied.
 int launch_filter(lamino_plan_t p, const void* d, int dtype, float* q, int kind,
-                  cudaStream_t s);
+                  cudaStream_t s, long row0 = 0, long row1 = -1);
 int validate_dtype_kind(lamino_plan_t p, int dtype, int kind);
 int launch_rowfft(lamino_plan_t p, const void* d, int dtype, float2* R, int kind /* -1: no filter */,
-                  cudaStream_t s);
+                  cudaStream_t s, long row0 = 0, long row1 = -1);
+// The Fourier form after the row pass, stage by stage: column FFT of the
+// projections [k0, k1), gridding + x1 inverse FFT, x2 inverse FFT, and the x3
+// USFFT of the x2 rows [i10, i11) of the volume. run_fourier_after_rows runs
+// them all in order.
+int launch_colfft(lamino_plan_t p, int k0, int k1, cudaStream_t s);
+int launch_grid(lamino_plan_t p, cudaStream_t s);
+int launch_colifft(lamino_plan_t p, cudaStream_t s);
+int launch_zusfft(lamino_plan_t p, float* vol, int i10, int i11, cudaStream_t s);
 int run_fourier_after_rows(lamino_plan_t p, float* vol, cudaStream_t s);
 int launch_direct(lamino_plan_t p, const float* q, float* vol, cudaStream_t s);
 int launch_project_direct(lamino_plan_t p, const float* vol, float* d, cudaStream_t s);

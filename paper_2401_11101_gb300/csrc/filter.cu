@@ -41,15 +41,15 @@ __device__ __forceinline__ void load_pair_rows(const Tin* __restrict__ d, float2
 // One CTA handles `pairs` row pairs; each pair uses t = Wp/E threads.
 template <int E, typename Tin>
 __global__ void __launch_bounds__(512, 1) k_filter(const Tin* __restrict__ d, float* __restrict__ q,
-                                                long nrows, int W, FftDesc fp,
+                                                long row0, long row1, int W, FftDesc fp,
                                                 const float* __restrict__ filt, int pairs) {
     extern __shared__ float2 sm[];
     const int T = fp.t, N = fp.n;
     const int seq = threadIdx.x / T, tid = threadIdx.x % T;
     const long pair = (long)blockIdx.x * pairs + seq;
-    const long rA = 2 * pair, rB = 2 * pair + 1;
-    const bool active = seq < pairs && rA < nrows;
-    const bool hasB = rB < nrows;
+    const long rA = row0 + 2 * pair, rB = rA + 1;
+    const bool active = seq < pairs && rA < row1;
+    const bool hasB = rB < row1;
     float2* x = sm + (size_t)seq * fpad_len(N);
     if (active) load_pair_rows(d, x, rA, hasB, W, N, 0, tid, T);
     __syncthreads();
@@ -77,16 +77,16 @@ __global__ void __launch_bounds__(512, 1) k_filter(const Tin* __restrict__ d, fl
 // Output R[row][mi], row = k*H + r.
 template <int EP, int EF, typename Tin>
 __global__ void __launch_bounds__(512, 1) k_rowfft(const Tin* __restrict__ d, float2* __restrict__ R,
-                                                long nrows, int W, int offu, FftDesc fp, FftDesc ff,
-                                                const float* __restrict__ filt,
+                                                long row0, long row1, int W, int offu, FftDesc fp,
+                                                FftDesc ff, const float* __restrict__ filt,
                                                 const float2* __restrict__ phu, int pairs, int T) {
     extern __shared__ float2 sm[];
     const int Np = (EP > 0) ? fp.n : 0, Nf = ff.n;
     const int seq = threadIdx.x / T, tid = threadIdx.x % T;
     const long pair = (long)blockIdx.x * pairs + seq;
-    const long rA = 2 * pair, rB = 2 * pair + 1;
-    const bool active = seq < pairs && rA < nrows;
-    const bool hasB = rB < nrows;
+    const long rA = row0 + 2 * pair, rB = rA + 1;
+    const bool active = seq < pairs && rA < row1;
+    const bool hasB = rB < row1;
     const int Lp = (EP > 0) ? fpad_len(Np) : 0;
     float2* xp = sm + (size_t)seq * (Lp + fpad_len(Nf));
     float2* xf = xp + Lp;
@@ -140,10 +140,11 @@ int pairs_for(int T, size_t bytes_per_pair) {
 }
 
 template <typename Tin>
-int filter_typed(lamino_plan_t p, const Tin* d, float* q, int kind, cudaStream_t s) {
+int filter_typed(lamino_plan_t p, const Tin* d, float* q, int kind, cudaStream_t s, long row0,
+                 long row1) {
     const FftDesc& f = p->fWp;
-    long nrows = (long)p->nproj * p->H;
-    long npairs = (nrows + 1) / 2;
+    long npairs = (row1 - row0 + 1) / 2;
+    if (npairs <= 0) return LAMINO_OK;
     int pairs = pairs_for(f.t, sizeof(float2) * fpad_len(f.n));
     size_t smem = sizeof(float2) * fpad_len(f.n) * pairs;
     dim3 grid((unsigned)((npairs + pairs - 1) / pairs));
@@ -151,64 +152,70 @@ int filter_typed(lamino_plan_t p, const Tin* d, float* q, int kind, cudaStream_t
     ProfScope prof(p, "filter", s);
     if (f.e == 8) {
         cudaFuncSetAttribute(k_filter<8, Tin>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-        k_filter<8, Tin><<<grid, pairs * f.t, smem, s>>>(d, q, nrows, p->W, f, filt, pairs);
+        k_filter<8, Tin><<<grid, pairs * f.t, smem, s>>>(d, q, row0, row1, p->W, f, filt, pairs);
     } else {
         cudaFuncSetAttribute(k_filter<12, Tin>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-        k_filter<12, Tin><<<grid, pairs * f.t, smem, s>>>(d, q, nrows, p->W, f, filt, pairs);
+        k_filter<12, Tin><<<grid, pairs * f.t, smem, s>>>(d, q, row0, row1, p->W, f, filt, pairs);
     }
     LAM_LAUNCH_CHECK(p, "filter kernel");
     return LAMINO_OK;
 }
 
 template <int EP, int EF, typename Tin>
-int rowfft_launch(lamino_plan_t p, const Tin* d, float2* R, const float* filt, cudaStream_t s) {
+int rowfft_launch(lamino_plan_t p, const Tin* d, float2* R, const float* filt, cudaStream_t s,
+                  long row0, long row1) {
     const int Tp = (EP > 0) ? p->fWp.t : 0;
     const int T = std::max(Tp, p->fWf.t);
     const size_t per_pair = sizeof(float2) * ((EP > 0 ? fpad_len(p->Wp) : 0) + fpad_len(p->Wf));
     int pairs = pairs_for(T, per_pair);
-    long nrows = (long)p->nproj * p->H;
-    long npairs = (nrows + 1) / 2;
+    long npairs = (row1 - row0 + 1) / 2;
+    if (npairs <= 0) return LAMINO_OK;
     size_t smem = per_pair * pairs;
     dim3 grid((unsigned)((npairs + pairs - 1) / pairs));
     auto kern = k_rowfft<EP, EF, Tin>;
     cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     ProfScope prof(p, EP > 0 ? "filter_rowfft" : "rowfft", s);
-    kern<<<grid, pairs * T, smem, s>>>(d, R, nrows, p->W, p->offu, p->fWp, p->fWf, filt, p->d_phu,
-                                       pairs, T);
+    kern<<<grid, pairs * T, smem, s>>>(d, R, row0, row1, p->W, p->offu, p->fWp, p->fWf, filt,
+                                       p->d_phu, pairs, T);
     LAM_LAUNCH_CHECK(p, "row FFT kernel");
     return LAMINO_OK;
 }
 
 template <typename Tin>
-int rowfft_typed(lamino_plan_t p, const Tin* d, float2* R, int kind, cudaStream_t s) {
+int rowfft_typed(lamino_plan_t p, const Tin* d, float2* R, int kind, cudaStream_t s, long r0,
+                 long r1) {
     const float* filt = kind >= 0 ? p->d_filt + (size_t)kind * p->Wp : nullptr;
     const int ef = p->fWf.e;
     if (kind < 0) {
-        return ef == 8 ? rowfft_launch<0, 8, Tin>(p, d, R, filt, s)
-                        : rowfft_launch<0, 12, Tin>(p, d, R, filt, s);
+        return ef == 8 ? rowfft_launch<0, 8, Tin>(p, d, R, filt, s, r0, r1)
+                        : rowfft_launch<0, 12, Tin>(p, d, R, filt, s, r0, r1);
     }
     const int ep = p->fWp.e;
-    if (ep == 8 && ef == 8) return rowfft_launch<8, 8, Tin>(p, d, R, filt, s);
-    if (ep == 8 && ef == 12) return rowfft_launch<8, 12, Tin>(p, d, R, filt, s);
-    if (ep == 12 && ef == 8) return rowfft_launch<12, 8, Tin>(p, d, R, filt, s);
-    return rowfft_launch<12, 12, Tin>(p, d, R, filt, s);
+    if (ep == 8 && ef == 8) return rowfft_launch<8, 8, Tin>(p, d, R, filt, s, r0, r1);
+    if (ep == 8 && ef == 12) return rowfft_launch<8, 12, Tin>(p, d, R, filt, s, r0, r1);
+    if (ep == 12 && ef == 8) return rowfft_launch<12, 8, Tin>(p, d, R, filt, s, r0, r1);
+    return rowfft_launch<12, 12, Tin>(p, d, R, filt, s, r0, r1);
 }
 
 }  // namespace
 
-int launch_filter(lamino_plan_t p, const void* d, int dtype, float* q, int kind, cudaStream_t s) {
+int launch_filter(lamino_plan_t p, const void* d, int dtype, float* q, int kind, cudaStream_t s,
+                  long row0, long row1) {
+    if (row1 < 0) row1 = (long)p->nproj * p->H;
     switch (dtype) {
-        case LAMINO_F32: return filter_typed(p, (const float*)d, q, kind, s);
-        case LAMINO_F16: return filter_typed(p, (const __half*)d, q, kind, s);
-        default: return filter_typed(p, (const __nv_bfloat16*)d, q, kind, s);
+        case LAMINO_F32: return filter_typed(p, (const float*)d, q, kind, s, row0, row1);
+        case LAMINO_F16: return filter_typed(p, (const __half*)d, q, kind, s, row0, row1);
+        default: return filter_typed(p, (const __nv_bfloat16*)d, q, kind, s, row0, row1);
     }
 }
 
-int launch_rowfft(lamino_plan_t p, const void* d, int dtype, float2* R, int kind, cudaStream_t s) {
+int launch_rowfft(lamino_plan_t p, const void* d, int dtype, float2* R, int kind, cudaStream_t s,
+                  long row0, long row1) {
+    if (row1 < 0) row1 = (long)p->nproj * p->H;
     switch (dtype) {
-        case LAMINO_F32: return rowfft_typed(p, (const float*)d, R, kind, s);
-        case LAMINO_F16: return rowfft_typed(p, (const __half*)d, R, kind, s);
-        default: return rowfft_typed(p, (const __nv_bfloat16*)d, R, kind, s);
+        case LAMINO_F32: return rowfft_typed(p, (const float*)d, R, kind, s, row0, row1);
+        case LAMINO_F16: return rowfft_typed(p, (const __half*)d, R, kind, s, row0, row1);
+        default: return rowfft_typed(p, (const __nv_bfloat16*)d, R, kind, s, row0, row1);
     }
 }
 

@@ -29,12 +29,12 @@ namespace {
 // ---------------------------------------------------------------- colfft
 template <int E>
 __global__ void __launch_bounds__(512, 2) k_colfft(const float2* __restrict__ R, float2* __restrict__ G,
-                                                 float2* __restrict__ st,
+                                                 float2* __restrict__ st, int k0,
                                                  int nproj, int H, int Wf, int L, int offv, FftDesc fh,
                                                  const float2* __restrict__ phv, int C) {
     extern __shared__ float2 sm[];
     const int Hf = fh.n, ld = Hf + 1;
-    const int k = blockIdx.y, m0 = blockIdx.x * C;
+    const int k = k0 + blockIdx.y, m0 = blockIdx.x * C;
     // load C columns of projection k, zero-padded rows, into sequences of length Hf
     // (8 independent loads in flight per thread)
     constexpr int U = 8;
@@ -495,10 +495,10 @@ __global__ void __launch_bounds__(512, 2) k_zusfft(const float2* __restrict__ P,
                                                  int L, int n0, int n1, int n2, FftDesc f3,
                                                  const int* __restrict__ zoff, const int* __restrict__ zl,
                                                  const float* __restrict__ zw,
-                                                 const float* __restrict__ dec3, int C) {
+                                                 const float* __restrict__ dec3, int C, int i10) {
     extern __shared__ float2 sm[];
     const int M3 = f3.n, ld = M3 + 1;
-    const int i1 = blockIdx.y, i00 = blockIdx.x * C;
+    const int i1 = i10 + blockIdx.y, i00 = blockIdx.x * C;
     float2* Pl = sm;                   // [L][C]
     float2* U = sm + (size_t)L * C;    // [C][M3 + 1]
     constexpr int NB = 8;
@@ -791,31 +791,53 @@ int colfft_chunk(lamino_plan_t p) {
     return C;
 }
 
-int run_fourier_after_rows(lamino_plan_t p, float* vol, cudaStream_t s) {
-    float2* R = (float2*)p->ws_a;   // row spectra   [nproj][H][Wf]
-    float2* G = (float2*)p->ws_b;   // half spectra  [L][nproj][Wf]
-    float2* V = (float2*)p->ws_a;   // x1 pass       [L][n0][M2]   (R is dead by then)
-    float2* P = (float2*)p->ws_b;   // planes        [L][n1][n0]   (G is dead by then)
+// Workspace views of the Fourier form: row spectra R and, after the
+// gridding, the x1 pass V share workspace A; half spectra G (+ the chunk
+// statistics after them) and, after the x2 pass, the planes P share B.
+struct FourierBufs {
+    float2 *R, *G, *st, *V, *P;
+    int CH;
+};
+static FourierBufs fourier_bufs(lamino_plan_t p) {
+    FourierBufs b;
+    b.R = (float2*)p->ws_a;    // [nproj][H][Wf]
+    b.G = (float2*)p->ws_b;    // [L][nproj][Wf]
+    b.V = (float2*)p->ws_a;    // [L][n0][M2]   (R is dead by then)
+    b.P = (float2*)p->ws_b;    // [L][n1][n0]   (G is dead by then)
+    b.CH = colfft_chunk(p);
+    b.st = b.G + (size_t)p->L * p->nproj * p->Wf;
+    return b;
+}
 
+int launch_colfft(lamino_plan_t p, int k0, int k1, cudaStream_t s) {
+    if (k1 <= k0) return LAMINO_OK;
+    const FourierBufs fb = fourier_bufs(p);
+    float2 *R = fb.R, *G = fb.G, *st = fb.st;
+    const int CH = fb.CH;
     // column FFT (+ chunk statistics for the gridding bound, after G in B)
-    const int CH = colfft_chunk(p);
-    float2* st = G + (size_t)p->L * p->nproj * p->Wf;
     {
         const FftDesc& f = p->fHf;
         const int C = CH;
         size_t smem = (size_t)C * (f.n + 1) * sizeof(float2);
-        dim3 grid(p->Wf / C, p->nproj);
+        dim3 grid(p->Wf / C, k1 - k0);
         int threads = std::min(512, std::max(C * f.t, 128));
         ProfScope prof(p, "colfft", s);
         if (f.e == 8) {
             set_smem(k_colfft<8>, smem);
-            k_colfft<8><<<grid, threads, smem, s>>>(R, G, st, p->nproj, p->H, p->Wf, p->L, p->offv, f, p->d_phv, C);
+            k_colfft<8><<<grid, threads, smem, s>>>(R, G, st, k0, p->nproj, p->H, p->Wf, p->L, p->offv, f, p->d_phv, C);
         } else {
             set_smem(k_colfft<12>, smem);
-            k_colfft<12><<<grid, threads, smem, s>>>(R, G, st, p->nproj, p->H, p->Wf, p->L, p->offv, f, p->d_phv, C);
+            k_colfft<12><<<grid, threads, smem, s>>>(R, G, st, k0, p->nproj, p->H, p->Wf, p->L, p->offv, f, p->d_phv, C);
         }
         LAM_LAUNCH_CHECK(p, "column FFT kernel");
     }
+    return LAMINO_OK;
+}
+
+int launch_grid(lamino_plan_t p, cudaStream_t s) {
+    const FourierBufs fb = fourier_bufs(p);
+    float2 *G = fb.G, *st = fb.st, *V = fb.V;
+    const int CH = fb.CH;
     // gridding + x1 inverse FFT
     {
         GridArgs a;
@@ -851,6 +873,12 @@ int run_fourier_after_rows(lamino_plan_t p, float* vol, cudaStream_t s) {
         else dispatch_grid_w<12>(p->w, a, grid, threads, smem, s);
         LAM_LAUNCH_CHECK(p, "gridding kernel");
     }
+    return LAMINO_OK;
+}
+
+int launch_colifft(lamino_plan_t p, cudaStream_t s) {
+    const FourierBufs fb = fourier_bufs(p);
+    float2 *V = fb.V, *P = fb.P;
     // x2 inverse FFT
     {
         const FftDesc& f = p->fM2;
@@ -871,6 +899,13 @@ int run_fourier_after_rows(lamino_plan_t p, float* vol, cudaStream_t s) {
         }
         LAM_LAUNCH_CHECK(p, "x2 inverse FFT kernel");
     }
+    return LAMINO_OK;
+}
+
+int launch_zusfft(lamino_plan_t p, float* vol, int i10, int i11, cudaStream_t s) {
+    if (i11 <= i10) return LAMINO_OK;
+    const FourierBufs fb = fourier_bufs(p);
+    float2* P = fb.P;
     // x3 USFFT
     {
         const FftDesc& f = p->fM3;
@@ -878,21 +913,29 @@ int run_fourier_after_rows(lamino_plan_t p, float* vol, cudaStream_t s) {
         auto bytes = [&](int c) { return (size_t)c * ((size_t)p->L + f.n + 1) * sizeof(float2); };
         while (C > 1 && bytes(C) > 72 * 1024) C /= 2;
         size_t smem = bytes(C);
-        dim3 grid((p->n0 + C - 1) / C, p->n1);
+        dim3 grid((p->n0 + C - 1) / C, i11 - i10);
         int threads = std::min(512, std::max(128, C * f.t));
         ProfScope prof(p, "zusfft", s);
         if (f.e == 8) {
             set_smem(k_zusfft<8>, smem);
             k_zusfft<8><<<grid, threads, smem, s>>>(P, vol, p->L, p->n0, p->n1, p->n2, f, p->d_zoff,
-                                                     p->d_zl, p->d_zw, p->d_dec3, C);
+                                                     p->d_zl, p->d_zw, p->d_dec3, C, i10);
         } else {
             set_smem(k_zusfft<12>, smem);
             k_zusfft<12><<<grid, threads, smem, s>>>(P, vol, p->L, p->n0, p->n1, p->n2, f, p->d_zoff,
-                                                     p->d_zl, p->d_zw, p->d_dec3, C);
+                                                     p->d_zl, p->d_zw, p->d_dec3, C, i10);
         }
         LAM_LAUNCH_CHECK(p, "x3 USFFT kernel");
     }
     return LAMINO_OK;
+}
+
+int run_fourier_after_rows(lamino_plan_t p, float* vol, cudaStream_t s) {
+    int rc;
+    if ((rc = launch_colfft(p, 0, p->nproj, s))) return rc;
+    if ((rc = launch_grid(p, s))) return rc;
+    if ((rc = launch_colifft(p, s))) return rc;
+    return launch_zusfft(p, vol, 0, p->n1, s);
 }
 
 

@@ -195,6 +195,8 @@ void free_plan(lamino_plan_t p) {
     for (void* b : bufs)
         if (b) cudaFree(b);
     for (cudaEvent_t e : p->ev_pool) cudaEventDestroy(e);
+    for (cudaEvent_t e : p->pipe_ev) cudaEventDestroy(e);
+    if (p->copy_stream) cudaStreamDestroy(p->copy_stream);
     delete p;
 }
 
@@ -532,6 +534,23 @@ int lamino_fbp(lamino_plan_t p, int form, const void* d, int dtype, float* vol, 
     return launch_direct(p, p->q_buf, vol, stream);
 }
 
+// Host pipeline of lamino_fbp_host: the projections go up in chunks of whole
+// projections on a copy stream while the row (and, for the Fourier form,
+// column) passes of the chunks already copied run on the caller's stream; the
+// Fourier volume comes back in slabs of x2 rows while the x3 pass computes the
+// next slab. Every dependency is an event; the call returns after both
+// streams have drained.
+static int ensure_pipeline(lamino_plan_t p, size_t nev) {
+    if (!p->copy_stream)
+        LAM_CUDA(p, cudaStreamCreateWithFlags(&p->copy_stream, cudaStreamNonBlocking));
+    while (p->pipe_ev.size() < nev) {
+        cudaEvent_t e;
+        LAM_CUDA(p, cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
+        p->pipe_ev.push_back(e);
+    }
+    return LAMINO_OK;
+}
+
 int lamino_fbp_host(lamino_plan_t p, int form, const void* d_host, int dtype, float* vol_host,
                     int kind, cudaStream_t stream) {
     if (!p) return fail(nullptr, LAMINO_EINVAL, "NULL plan");
@@ -539,14 +558,75 @@ int lamino_fbp_host(lamino_plan_t p, int form, const void* d_host, int dtype, fl
     int rc = validate_dtype_kind(p, dtype, kind);
     if (rc) return rc;
     if ((rc = set_device(p))) return rc;
-    size_t esz = dtype == LAMINO_F32 ? 4 : 2;
-    size_t din = esz * (size_t)p->nproj * p->H * p->W;
-    size_t dvol = sizeof(float) * (size_t)p->n0 * p->n1 * p->n2;
+    if (form != LAMINO_FOURIER && form != LAMINO_DIRECT) return fail(p, LAMINO_EINVAL, "unknown form %d", form);
+    if (form == LAMINO_FOURIER) {
+        if (!p->fourier_ok) return fail(p, LAMINO_EUNSUPPORTED, "%s", p->fourier_why.c_str());
+    }
+    if (!p->filter_ok) return fail(p, LAMINO_EUNSUPPORTED, "filter length %d is not a supported FFT length", p->Wp);
+    const size_t esz = dtype == LAMINO_F32 ? 4 : 2;
+    const size_t proj_bytes = esz * (size_t)p->H * p->W;
+    const size_t din = proj_bytes * p->nproj;
+    const size_t dvol = sizeof(float) * (size_t)p->n0 * p->n1 * p->n2;
     if ((rc = ensure_buffer(p, &p->h_in, &p->h_in_bytes, din, "device copy of projections"))) return rc;
     if ((rc = ensure_buffer(p, (void**)&p->h_vol, &p->h_vol_bytes, dvol, "device volume"))) return rc;
-    LAM_CUDA(p, cudaMemcpyAsync(p->h_in, d_host, din, cudaMemcpyHostToDevice, stream));
-    if ((rc = lamino_fbp(p, form, p->h_in, dtype, p->h_vol, kind, stream))) return rc;
-    LAM_CUDA(p, cudaMemcpyAsync(vol_host, p->h_vol, dvol, cudaMemcpyDeviceToHost, stream));
+    if (form == LAMINO_FOURIER) {
+        size_t a, b;
+        fourier_workspace(p, &a, &b);
+        if ((rc = ensure_buffer(p, &p->ws_a, &p->ws_a_bytes, a, "Fourier workspace A"))) return rc;
+        if ((rc = ensure_buffer(p, &p->ws_b, &p->ws_b_bytes, b, "Fourier workspace B"))) return rc;
+    } else {
+        size_t need = sizeof(float) * (size_t)p->nproj * p->H * p->W;
+        if ((rc = ensure_buffer(p, (void**)&p->q_buf, &p->q_buf_bytes, need, "filtered rows"))) return rc;
+    }
+    const int nin = std::min(8, p->nproj);                          // projection chunks
+    const int nout = form == LAMINO_FOURIER ? std::min(8, p->n1) : 1;   // volume slabs
+    if ((rc = ensure_pipeline(p, (size_t)nin + nout + 2))) return rc;
+    cudaEvent_t* ev = p->pipe_ev.data();
+    cudaStream_t cs = p->copy_stream;
+    // the copies start after whatever the caller queued before (which may
+    // still read the plan's buffers)
+    LAM_CUDA(p, cudaEventRecord(ev[0], stream));
+    LAM_CUDA(p, cudaStreamWaitEvent(cs, ev[0], 0));
+    for (int c = 0; c < nin; ++c) {
+        const long k0 = (long)p->nproj * c / nin, k1 = (long)p->nproj * (c + 1) / nin;
+        LAM_CUDA(p, cudaMemcpyAsync((char*)p->h_in + k0 * proj_bytes, (const char*)d_host + k0 * proj_bytes,
+                                    (k1 - k0) * proj_bytes, cudaMemcpyHostToDevice, cs));
+        LAM_CUDA(p, cudaEventRecord(ev[1 + c], cs));
+    }
+    for (int c = 0; c < nin; ++c) {
+        const long k0 = (long)p->nproj * c / nin, k1 = (long)p->nproj * (c + 1) / nin;
+        LAM_CUDA(p, cudaStreamWaitEvent(stream, ev[1 + c], 0));
+        if (form == LAMINO_FOURIER) {
+            if ((rc = launch_rowfft(p, p->h_in, dtype, (float2*)p->ws_a, kind, stream, k0 * p->H, k1 * p->H)))
+                return rc;
+            if ((rc = launch_colfft(p, (int)k0, (int)k1, stream))) return rc;
+        } else {
+            if ((rc = launch_filter(p, p->h_in, dtype, p->q_buf, kind, stream, k0 * p->H, k1 * p->H)))
+                return rc;
+        }
+    }
+    cudaEvent_t* evo = ev + 1 + nin;
+    if (form == LAMINO_FOURIER) {
+        if ((rc = launch_grid(p, stream))) return rc;
+        if ((rc = launch_colifft(p, stream))) return rc;
+        const size_t row = sizeof(float) * (size_t)p->n0, slice = row * p->n1;
+        for (int v = 0; v < nout; ++v) {
+            const int i10 = (int)((long)p->n1 * v / nout), i11 = (int)((long)p->n1 * (v + 1) / nout);
+            if ((rc = launch_zusfft(p, p->h_vol, i10, i11, stream))) return rc;
+            LAM_CUDA(p, cudaEventRecord(evo[v], stream));
+            LAM_CUDA(p, cudaStreamWaitEvent(cs, evo[v], 0));
+            // slab [x3][x2 in i10..i11)[x1]: n2 pieces of (i11 - i10) rows
+            LAM_CUDA(p, cudaMemcpy2DAsync((char*)vol_host + i10 * row, slice, (const char*)p->h_vol + i10 * row,
+                                          slice, (i11 - i10) * row, p->n2, cudaMemcpyDeviceToHost, cs));
+        }
+    } else {
+        if ((rc = launch_direct(p, p->q_buf, p->h_vol, stream))) return rc;
+        LAM_CUDA(p, cudaEventRecord(evo[0], stream));
+        LAM_CUDA(p, cudaStreamWaitEvent(cs, evo[0], 0));
+        LAM_CUDA(p, cudaMemcpyAsync(vol_host, p->h_vol, dvol, cudaMemcpyDeviceToHost, cs));
+    }
+    LAM_CUDA(p, cudaEventRecord(evo[nout], cs));
+    LAM_CUDA(p, cudaStreamWaitEvent(stream, evo[nout], 0));
     LAM_CUDA(p, cudaStreamSynchronize(stream));
     return LAMINO_OK;
 }
