@@ -34,8 +34,8 @@ bool fft_len_ok(int n);
 int fft_size_at_least(double n);   // smallest 2^k or 3*2^k >= n
 
 struct DirectCfg {
-    int tx = 32, ty = 8, tz = 32;    // voxel tile of one CTA (x1, x2, x3)
-    int bw = 0, bh = 0;              // TMA box (detector columns, rows)
+    int tx = 32, ty = 16, tz = 16;   // voxel tile of one CTA (x1, x2, x3)
+    int bw = 0, bh = 0;              // detector footprint box (columns, rows)
     int stages = 6;                  // TMA pipeline depth
 };
 
@@ -80,7 +80,8 @@ struct lamino_plan_s {
     cudaStream_t copy_stream = nullptr;            // host pipeline: copies overlap kernels
     std::vector<cudaEvent_t> pipe_ev;              // host pipeline: chunk events
 
-    lam::DirectCfg dcfg;
+    lam::DirectCfg dcfg;           // backprojector (k_direct): 32 x 16 x 16 tile, TMA box
+    lam::DirectCfg pcfg;           // direct projector (k_project): 32 x 8 x 32 tile
     bool filter_ok = false;        // Wp is a supported FFT length
     bool fourier_ok = false;       // Wf, Hf, M1..M3 supported and n even
     std::string fourier_why;

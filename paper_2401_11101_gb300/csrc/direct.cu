@@ -25,9 +25,40 @@
 namespace lam {
 namespace {
 
+// Backprojector tile: BX x BY columns x BZ slices; each of the 256 consumer
+// threads owns two columns (x2 = y and y + BY/2) whose updates run as packed
+// f32x2 arithmetic. Projector tile (k_project): TX x TY columns x TZ slices.
+constexpr int BX = 32, BY = 16, BZ = 16;
 constexpr int TX = 32, TY = 8, TZ = 32;
-constexpr int kConsumers = TX * TY;              // 256 threads, 8 warps
+constexpr int kConsumers = 256;                  // 8 warps
 constexpr int kThreads = kConsumers + 32;        // + 1 producer warp
+static_assert(BX * BY == 2 * kConsumers && TX * TY == kConsumers, "thread layout");
+
+// packed pairs of floats (one 64-bit register pair) and f32x2 arithmetic
+__device__ __forceinline__ unsigned long long pk(float a, float b) {
+    unsigned long long r;
+    asm("mov.b64 %0, {%1, %2};" : "=l"(r) : "f"(a), "f"(b));
+    return r;
+}
+__device__ __forceinline__ void upk(unsigned long long r, float& a, float& b) {
+    asm("mov.b64 {%0, %1}, %2;" : "=f"(a), "=f"(b) : "l"(r));
+}
+__device__ __forceinline__ unsigned long long add2(unsigned long long a, unsigned long long b) {
+    unsigned long long r;
+    asm("add.rn.f32x2 %0, %1, %2;" : "=l"(r) : "l"(a), "l"(b));
+    return r;
+}
+__device__ __forceinline__ unsigned long long sub2(unsigned long long a, unsigned long long b) {
+    unsigned long long r;
+    asm("sub.rn.f32x2 %0, %1, %2;" : "=l"(r) : "l"(a), "l"(b));
+    return r;
+}
+__device__ __forceinline__ unsigned long long fma2(unsigned long long a, unsigned long long b,
+                                                   unsigned long long c) {
+    unsigned long long r;
+    asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(r) : "l"(a), "l"(b), "l"(c));
+    return r;
+}
 
 struct StageMeta {
     float jb, rb;       // tile origin (x1 = X0, x2 = Y0, x3 = Z0) in box coordinates
@@ -60,7 +91,7 @@ __global__ void __launch_bounds__(kThreads) k_direct(const __grid_constant__ CUt
     extern __shared__ __align__(128) unsigned char dsm[];
     float* tiles = reinterpret_cast<float*>(dsm);
     StageMeta* meta = reinterpret_cast<StageMeta*>(
-        dsm + sizeof(float) * ((size_t)a.stages * a.stage_floats + (size_t)(TZ + 2) * a.bw));
+        dsm + sizeof(float) * ((size_t)a.stages * a.stage_floats + (size_t)(BZ + 2) * a.bw));
     uint64_t* full = reinterpret_cast<uint64_t*>(meta + a.stages);
     uint64_t* empty = full + a.stages;
     const int S = a.stages;
@@ -74,7 +105,7 @@ __global__ void __launch_bounds__(kThreads) k_direct(const __grid_constant__ CUt
     }
     __syncthreads();
 
-    const int X0i = blockIdx.x * TX, Y0i = blockIdx.y * TY, Z0i = blockIdx.z * TZ;
+    const int X0i = blockIdx.x * BX, Y0i = blockIdx.y * BY, Z0i = blockIdx.z * BZ;
     if (threadIdx.x >= kConsumers) {
         // ---------------- producer warp (lane 0 issues) ----------------
         if (threadIdx.x != kConsumers) return;
@@ -92,9 +123,9 @@ __global__ void __launch_bounds__(kThreads) k_direct(const __grid_constant__ CUt
             const double ct = a.trig64[2 * k], st = a.trig64[2 * k + 1];
             const double cj1 = ct, cj2 = st;                          // j = cj1 x1 + cj2 x2 + W/2
             const double cr1 = st * a.sp, cr2 = -ct * a.sp, cr3 = a.cp; // r = cr.x + H/2
-            double jmin = 0.5 * a.W + cj1 * (cj1 >= 0 ? X0 : X0 + TX - 1) + cj2 * (cj2 >= 0 ? Y0 : Y0 + TY - 1);
-            double rmin = 0.5 * a.H + cr1 * (cr1 >= 0 ? X0 : X0 + TX - 1) +
-                          cr2 * (cr2 >= 0 ? Y0 : Y0 + TY - 1) + cr3 * (cr3 >= 0 ? Z0 : Z0 + TZ - 1);
+            double jmin = 0.5 * a.W + cj1 * (cj1 >= 0 ? X0 : X0 + BX - 1) + cj2 * (cj2 >= 0 ? Y0 : Y0 + BY - 1);
+            double rmin = 0.5 * a.H + cr1 * (cr1 >= 0 ? X0 : X0 + BX - 1) +
+                          cr2 * (cr2 >= 0 ? Y0 : Y0 + BY - 1) + cr3 * (cr3 >= 0 ? Z0 : Z0 + BZ - 1);
             // one guard column/row before the footprint keeps every rounded
             // coordinate >= 1 inside the box
             int js = (int)floor(jmin) - 1;
@@ -121,14 +152,16 @@ __global__ void __launch_bounds__(kThreads) k_direct(const __grid_constant__ CUt
     }
 
     // ---------------- consumers ----------------
-    // a warp covers an 8 x 4 patch of columns: its lanes then sample at most
-    // ~5 detector rows instead of up to 11
+    // a warp covers an 8 x 4 patch of columns (and the patch 8 rows of x2
+    // further): its lanes then sample at most ~5 detector rows per load
     const int lane = threadIdx.x & 31, wq = threadIdx.x >> 5;
     const int tx = (lane & 7) + 8 * (wq & 3), ty = (lane >> 3) + 4 * (wq >> 2);
-    float acc[TZ];
+    constexpr int DY = BY / 2;                  // second column: x2 = ty + DY
+    unsigned long long acc[BZ];                 // (column ty, column ty + DY) per slice
 #pragma unroll
-    for (int z = 0; z < TZ; ++z) acc[z] = 0.f;
+    for (int z = 0; z < BZ; ++z) acc[z] = 0ull;   // +0.0f in both halves
     const float cpf = a.cpf;
+    const unsigned long long cpf2 = pk(cpf, cpf);
     const int bw = a.bw, bh = a.bh;
     for (int k = 0; k < a.nproj; ++k) {
         const int s = k % S;
@@ -138,41 +171,68 @@ __global__ void __launch_bounds__(kThreads) k_direct(const __grid_constant__ CUt
         }
         const StageMeta m = meta[s];
         const float* tile = tiles + (size_t)s * a.stage_floats;
-        const float jl = m.jb + m.ct * (float)tx + m.st * (float)ty;
-        const float jf = floorf(jl);
-        const float fj = jl - jf;
-        const int j0 = min(max((int)jf, 0), bw - 2);
-        // row walk: r(z) = rl + cos(phi) z advances by at most one row per slice
-        const float rl = m.rb + m.stsp * (float)tx - m.ctsp * (float)ty;
-        const float rf = floorf(rl);
-        float fr = rl - rf;
-        int r0 = (int)rf;
-        // the walk adds at most TZ rows; the stage buffers carry TZ + 2 rows of
-        // slack after the last stage, so every read stays inside shared memory
-        r0 = min(max(r0, 0), bh - 2);
-        const float* p = tile + j0 + r0 * bw;
-        float h_lo = fmaf(fj, p[1] - p[0], p[0]);              // row r0, lerped in u
-        p += bw;                                               // row r0 + 1
-        float h_hi = fmaf(fj, p[1] - p[0], p[0]);
+        // per column: detector column j (constant along x3) and the row walk
+        // r(z) = rl + cos(phi) z, which advances by at most one row per slice
+        float fj[2], fr[2];
+        const float* p[2];
+        float lo[2], hi[2];
 #pragma unroll
-        for (int z = 0; z < TZ; ++z) {
-            acc[z] += fmaf(fr, h_hi - h_lo, h_lo);
-            fr += cpf;
-            const bool adv = fr >= 1.f;
-            fr = adv ? fr - 1.f : fr;
-            p += adv ? bw : 0;
-            h_lo = adv ? h_hi : h_lo;
-            h_hi = fmaf(fj, p[1] - p[0], p[0]);
+        for (int c = 0; c < 2; ++c) {
+            const float y = (float)(ty + c * DY);
+            const float jl = m.jb + m.ct * (float)tx + m.st * y;
+            const float jf = floorf(jl);
+            fj[c] = jl - jf;
+            const int j0 = min(max((int)jf, 0), bw - 2);
+            const float rl = m.rb + m.stsp * (float)tx - m.ctsp * y;
+            const float rf = floorf(rl);
+            fr[c] = rl - rf;
+            // the walk adds at most BZ rows; the stage buffers carry BZ + 2
+            // rows of slack after the last stage, so every read stays inside
+            // shared memory
+            const int r0 = min(max((int)rf, 0), bh - 2);
+            const float* q = tile + j0 + r0 * bw;
+            lo[c] = fmaf(fj[c], q[1] - q[0], q[0]);             // row r0, lerped in u
+            q += bw;                                              // row r0 + 1
+            hi[c] = fmaf(fj[c], q[1] - q[0], q[0]);
+            p[c] = q;
+        }
+        const unsigned long long fj2 = pk(fj[0], fj[1]);
+        unsigned long long fr2 = pk(fr[0], fr[1]);
+        unsigned long long hlo = pk(lo[0], lo[1]), hhi = pk(hi[0], hi[1]);
+#pragma unroll
+        for (int z = 0; z < BZ; ++z) {
+            acc[z] = add2(acc[z], fma2(fr2, sub2(hhi, hlo), hlo));
+            fr2 = add2(fr2, cpf2);
+            float f0, f1, h0, h1, l0, l1;
+            upk(fr2, f0, f1);
+            upk(hhi, h0, h1);
+            upk(hlo, l0, l1);
+            const bool a0 = f0 >= 1.f, a1 = f1 >= 1.f;
+            f0 = a0 ? f0 - 1.f : f0;
+            f1 = a1 ? f1 - 1.f : f1;
+            p[0] += a0 ? bw : 0;
+            p[1] += a1 ? bw : 0;
+            l0 = a0 ? h0 : l0;
+            l1 = a1 ? h1 : l1;
+            fr2 = pk(f0, f1);
+            hlo = pk(l0, l1);
+            const unsigned long long s0 = pk(p[0][0], p[1][0]), s1 = pk(p[0][1], p[1][1]);
+            hhi = fma2(fj2, sub2(s1, s0), s0);
         }
         __syncwarp();
         if (lane == 0) mbar_arrive(smem_addr(empty + s));
     }
-    const int i0 = X0i + tx, i1 = Y0i + ty;
-    if (i0 < a.n0 && i1 < a.n1) {
+    const int i0 = X0i + tx;
 #pragma unroll
-        for (int z = 0; z < TZ; ++z) {
+    for (int c = 0; c < 2; ++c) {
+        const int i1 = Y0i + ty + c * DY;
+        if (i0 >= a.n0 || i1 >= a.n1) continue;
+#pragma unroll
+        for (int z = 0; z < BZ; ++z) {
+            float v0, v1;
+            upk(acc[z], v0, v1);
             const int i2 = Z0i + z;
-            if (i2 < a.n2) a.vol[((size_t)i2 * a.n1 + i1) * a.n0 + i0] = acc[z] * a.scale;
+            if (i2 < a.n2) a.vol[((size_t)i2 * a.n1 + i1) * a.n0 + i0] = (c == 0 ? v0 : v1) * a.scale;
         }
     }
 }
@@ -248,13 +308,13 @@ PFN_cuTensorMapEncodeTiled_v12000 get_encode() {
     return fn;
 }
 
-DirectArgs make_args(lamino_plan_t p) {
+DirectArgs make_args(lamino_plan_t p, const DirectCfg& cfg) {
     DirectArgs a;
     a.trig64 = p->d_trig64;
     a.vol = nullptr;
     a.err = p->d_err;
     a.nproj = p->nproj; a.n0 = p->n0; a.n1 = p->n1; a.n2 = p->n2; a.W = p->W; a.H = p->H;
-    a.bw = p->dcfg.bw; a.bh = p->dcfg.bh; a.stages = p->dcfg.stages;
+    a.bw = cfg.bw; a.bh = cfg.bh; a.stages = cfg.stages;
     a.stage_floats = (a.bw * a.bh + 31) / 32 * 32;   // 128-byte aligned stages
     a.sp = sin(p->tilt);
     a.cp = cos(p->tilt);
@@ -291,11 +351,11 @@ int launch_direct(lamino_plan_t p, const float* q, float* vol, cudaStream_t s) {
                          CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
                          CU_TENSOR_MAP_L2_PROMOTION_L2_128B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
     if (cr != CUDA_SUCCESS) return fail(p, LAMINO_ECUDA, "cuTensorMapEncodeTiled failed (%d)", (int)cr);
-    DirectArgs a = make_args(p);
+    DirectArgs a = make_args(p, p->dcfg);
     a.vol = vol;
-    size_t smem = sizeof(float) * ((size_t)a.stages * a.stage_floats + (size_t)(TZ + 2) * a.bw) +
+    size_t smem = sizeof(float) * ((size_t)a.stages * a.stage_floats + (size_t)(BZ + 2) * a.bw) +
                   sizeof(StageMeta) * a.stages + 2 * sizeof(uint64_t) * a.stages;
-    dim3 grid((p->n0 + TX - 1) / TX, (p->n1 + TY - 1) / TY, (p->n2 + TZ - 1) / TZ);
+    dim3 grid((p->n0 + BX - 1) / BX, (p->n1 + BY - 1) / BY, (p->n2 + BZ - 1) / BZ);
     cudaFuncSetAttribute(k_direct, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     ProfScope prof(p, "direct", s);
     k_direct<<<grid, kThreads, smem, s>>>(map, a);
@@ -305,8 +365,7 @@ int launch_direct(lamino_plan_t p, const float* q, float* vol, cudaStream_t s) {
 
 int launch_project_direct(lamino_plan_t p, const float* vol, float* d, cudaStream_t s) {
     LAM_CUDA(p, cudaMemsetAsync(d, 0, sizeof(float) * (size_t)p->nproj * p->H * p->W, s));
-    DirectArgs a = make_args(p);
-    // the footprint box here needs no alignment slack but keep the same size
+    DirectArgs a = make_args(p, p->pcfg);
     size_t smem = sizeof(float) * (size_t)a.bw * a.bh;
     dim3 grid((p->n0 + TX - 1) / TX, (p->n1 + TY - 1) / TY, (p->n2 + TZ - 1) / TZ);
     cudaFuncSetAttribute(k_project, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);

@@ -329,15 +329,23 @@ int build_tables(lamino_plan_t p) {
 // tile (tx x ty columns, tz slices) at any angle, plus the bilinear
 // neighbour, one guard column/row before the footprint, and alignment slack
 // of the box start (x rounded down to a multiple of 4).
-void direct_config(lamino_plan_t p) {
-    DirectCfg& c = p->dcfg;
+void box_for(DirectCfg& c, double tilt) {
     double diag = sqrt((double)(c.tx - 1) * (c.tx - 1) + (double)(c.ty - 1) * (c.ty - 1));
     int need_w = (int)floor(diag) + 1 /*guard*/ + 2 /*floor+neighbour*/ + 3 /*align*/ + 1;
     c.bw = (need_w + 3) / 4 * 4;
     // row pitch = 12 or 20 mod 32 words: rows 1..7 apart fall in different banks
     while (c.bw % 32 != 12 && c.bw % 32 != 20) c.bw += 4;
-    double span_r = fabs(sin(p->tilt)) * diag + cos(p->tilt) * (c.tz - 1);
+    double span_r = fabs(sin(tilt)) * diag + cos(tilt) * (c.tz - 1);
     c.bh = (int)floor(span_r) + 1 /*guard*/ + 2 /*floor+neighbour*/ + 2;
+}
+
+void direct_config(lamino_plan_t p) {
+    p->dcfg = DirectCfg();                      // 32 x 16 x 16
+    box_for(p->dcfg, p->tilt);
+    p->pcfg = DirectCfg();
+    p->pcfg.ty = 8;
+    p->pcfg.tz = 32;
+    box_for(p->pcfg, p->tilt);
 }
 
 }  // namespace
@@ -451,7 +459,7 @@ int lamino_plan(lamino_plan_t* out, int n0, int n1, int n2, int nproj, int det_w
         }
     }
     direct_config(p);
-    if (p->dcfg.bh > 256 || p->dcfg.bw > 256) {
+    if (p->dcfg.bh > 256 || p->dcfg.bw > 256 || p->pcfg.bh > 256 || p->pcfg.bw > 256) {
         free_plan(p);
         return fail(nullptr, LAMINO_EUNSUPPORTED, "detector footprint tile too large");
     }
