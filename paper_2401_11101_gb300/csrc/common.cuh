@@ -75,6 +75,7 @@ struct lamino_plan_s {
     void* ws_a = nullptr; size_t ws_a_bytes = 0;   // row spectra R / gridded planes V
     void* ws_b = nullptr; size_t ws_b_bytes = 0;   // half spectra G / planes P
     float* q_buf = nullptr; size_t q_buf_bytes = 0; // filtered rows (direct FBP)
+    float* q_pad = nullptr; size_t q_pad_bytes = 0; // rows padded to a 16-byte pitch (TMA)
     void* h_in = nullptr; size_t h_in_bytes = 0;   // device copy of host input
     float* h_vol = nullptr; size_t h_vol_bytes = 0;
     cudaStream_t copy_stream = nullptr;            // host pipeline: copies overlap kernels

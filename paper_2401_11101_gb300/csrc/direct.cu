@@ -332,13 +332,12 @@ int launch_direct(lamino_plan_t p, const float* q, float* vol, cudaStream_t s) {
     if ((p->W % 4) || ((uintptr_t)q % 16)) {
         pitch = (p->W + 3) / 4 * 4;
         size_t need = sizeof(float) * (size_t)p->nproj * p->H * pitch;
-        int rc = ensure_buffer(p, (void**)&p->q_buf, &p->q_buf_bytes, need, "padded projections");
+        int rc = ensure_buffer(p, (void**)&p->q_pad, &p->q_pad_bytes, need, "padded projections");
         if (rc) return rc;
-        if (p->q_buf == q) return fail(p, LAMINO_EUNSUPPORTED, "unaligned input aliases the plan buffer");
-        LAM_CUDA(p, cudaMemsetAsync(p->q_buf, 0, need, s));
-        LAM_CUDA(p, cudaMemcpy2DAsync(p->q_buf, sizeof(float) * pitch, q, sizeof(float) * p->W,
+        LAM_CUDA(p, cudaMemsetAsync(p->q_pad, 0, need, s));
+        LAM_CUDA(p, cudaMemcpy2DAsync(p->q_pad, sizeof(float) * pitch, q, sizeof(float) * p->W,
                                       sizeof(float) * p->W, (size_t)p->nproj * p->H, cudaMemcpyDeviceToDevice, s));
-        src = p->q_buf;
+        src = p->q_pad;
     }
     PFN_cuTensorMapEncodeTiled_v12000 encode = get_encode();
     if (!encode) return fail(p, LAMINO_ECUDA, "cuTensorMapEncodeTiled is not available from the driver");

@@ -191,7 +191,7 @@ int upload(lamino_plan_t p, T** dst, const std::vector<T>& v, const char* what) 
 void free_plan(lamino_plan_t p) {
     void* bufs[] = {p->d_trig, p->d_trig64, p->d_filt, p->d_phu, p->d_phv, p->d_dec1,
                     p->d_dec2, p->d_dec3, p->d_zoff, p->d_zl, p->d_zw, p->d_ztap, p->d_tw, p->d_err,
-                    p->ws_a, p->ws_b, p->q_buf, p->h_in, p->h_vol};
+                    p->ws_a, p->ws_b, p->q_buf, p->q_pad, p->h_in, p->h_vol};
     for (void* b : bufs)
         if (b) cudaFree(b);
     for (cudaEvent_t e : p->ev_pool) cudaEventDestroy(e);
@@ -664,6 +664,9 @@ int lamino_workspace_bytes(lamino_plan_t p, int form, size_t* bytes) {
         *bytes = a + b;
     } else if (form == LAMINO_DIRECT) {
         *bytes = sizeof(float) * (size_t)p->nproj * p->H * p->W;
+        // rows whose width is not a multiple of 4 floats are staged at a
+        // 16-byte pitch for the TMA loads
+        if (p->W % 4) *bytes += sizeof(float) * (size_t)p->nproj * p->H * ((p->W + 3) / 4 * 4);
     } else {
         return fail(p, LAMINO_EINVAL, "unknown form %d", form);
     }
