@@ -350,6 +350,26 @@ def rasterize_blobs(params: dict, geom: Geometry) -> np.ndarray:
     return out
 
 
+def rasterize_ellipsoids(params: dict, geom: Geometry, sub: int = 2) -> np.ndarray:
+    """The ellipsoid phantom averaged over sub^3 points per voxel, float64
+    [n2, n1, n0] (the sampled truth for reconstruction-quality checks)."""
+    o = (np.arange(sub) + 0.5) / sub - 0.5
+    out = np.zeros((geom.n2, geom.n1, geom.n0))
+    for a in o:
+        for b in o:
+            for c in o:
+                x1 = np.arange(geom.n0) - geom.n0 / 2.0 + a
+                x2 = np.arange(geom.n1) - geom.n1 / 2.0 + b
+                x3 = np.arange(geom.n2) - geom.n2 / 2.0 + c
+                X = np.stack(np.meshgrid(x1, x2, x3, indexing="ij"), -1)   # [n0, n1, n2, 3]
+                acc = np.zeros(X.shape[:3])
+                for M, cen, rho in zip(params["M"], params["centre"], params["rho"]):
+                    y = (X - cen) @ M.T
+                    acc += rho * ((y * y).sum(-1) <= 1.0)
+                out += acc.transpose(2, 1, 0)
+    return out / sub ** 3
+
+
 def random_projections(geom: Geometry, seed: int, dtype=np.float64) -> np.ndarray:
     """Plain seeded N(0,1) detector data [nproj, det_h, det_w] (for operator tests)."""
     rng = np.random.default_rng(seed)
