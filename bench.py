@@ -65,6 +65,8 @@ def parse():
     ap.add_argument("--no-serve", action="store_true")
     ap.add_argument("--serve-requests", type=int, default=32)
     ap.add_argument("--serve-rate", type=float, default=20.0)
+    ap.add_argument("--no-cg", action="store_true")
+    ap.add_argument("--cg-iters", type=int, default=50)
     return ap.parse_args()
 
 
@@ -240,6 +242,31 @@ def run_serving(n: int, rate: float, device: int, seed: int = 5) -> dict:
     return out
 
 
+# --------------------------------------------------------------------- CG
+
+def run_cg(iters: int, device: int) -> dict:
+    """CG least squares (Dai-Yuan directions, exact steps) with the Fourier-form
+    projector pair on the c4 workload: 256x256x128, 400 angles, det 128x384,
+    tilt 30 deg, Gaussian blobs, 0.5 % noise."""
+    from paper_2401_11101_gb300 import autograd as A, lamino as L
+    g, prm, d = I.make_projections("c4", device=f"cuda:{device}")
+    with L.Plan(g.n0, g.n1, g.n2, g.nproj, g.det_w, g.det_h, g.tilt) as p:
+        A.cg_least_squares(p, d, iters=2, form="fourier")        # warm-up
+        torch.cuda.synchronize()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record()
+        mu, hist = A.cg_least_squares(p, d, iters=iters, form="fourier")
+        b.record()
+        b.synchronize()
+        p.status()
+        ms = a.elapsed_time(b)
+    truth = torch.as_tensor(I.rasterize_blobs(prm, g), dtype=torch.float32, device=mu.device)
+    err = float((mu - truth).norm() / truth.norm())
+    return {"workload": "c4: " + WORKLOADS["c4"], "form": "fourier", "iterations": len(hist) - 1,
+            "ms_total": ms, "ms_per_iter": ms / max(1, len(hist) - 1),
+            "residual_ratio": hist[-1] / hist[0], "relL2_vs_phantom": err}
+
+
 # --------------------------------------------------------------------- arms
 
 def run_reference(args, geom, d):
@@ -388,6 +415,9 @@ def run_ours(args, geom, d):
     serve = None
     if not args.no_serve:
         serve = run_serving(args.serve_requests, args.serve_rate, local)
+    cg = None
+    if not args.no_cg:
+        cg = run_cg(args.cg_iters, local)
 
     cpu = None
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:
@@ -412,7 +442,7 @@ def run_ours(args, geom, d):
                           "fourier_over_direct": t_d / t_f},
                 "roofline": roof(dominant), "roofline_fourier": roof(dom_f),
                 "kernels": kernels, "gpu_launches": len(recs),
-                "clocks": clk, "e2e": e2e, "cpu_baseline": cpu, "serve": serve}
+                "clocks": clk, "e2e": e2e, "cpu_baseline": cpu, "serve": serve, "cg": cg}
         print(json.dumps(line), flush=True)
     plan.close()
 
