@@ -14,8 +14,12 @@
 
 namespace lam {
 
-// Largest FFT length any kernel handles (one sequence fits in shared memory).
+// Largest FFT length any kernel handles (one sequence fits in shared memory),
+// and the most threads one sequence may take (n / elements per thread): the
+// FFT kernels run blocks of at most 512 threads, and a block must hold at
+// least one whole sequence. So 2^k lengths go up to 4096, 3*2^k up to 6144.
 constexpr int kMaxFft = 8192;
+constexpr int kMaxFftThreads = 512;
 
 // Radix schedule of one FFT length: n = product of the stage radices, stage
 // st having radix (rads >> 4 st) & 15; power-of-two radices come first and a
@@ -346,6 +350,7 @@ template <int E>
 __device__ __forceinline__ void fft_many(float2* base, int ld, int nseq, const FftDesc& f, float s) {
     const int T = f.t;
     const int par = blockDim.x / T;
+    if (par == 0) return;   // a sequence needs more threads than the block has (the plan refuses this)
     const int g = threadIdx.x / T;
     const int mode = fft_group_mode(T);
     for (int s0 = 0; s0 < nseq; s0 += par) {
@@ -363,6 +368,7 @@ __device__ __forceinline__ void fft_many_planar(float* re, float* im, int ld, in
                                                 const FftDesc& f, float s) {
     const int T = f.t;
     const int par = blockDim.x / T;
+    if (par == 0) return;   // a sequence needs more threads than the block has (the plan refuses this)
     const int g = threadIdx.x / T;
     const int mode = fft_group_mode(T);
     for (int s0 = 0; s0 < nseq; s0 += par) {

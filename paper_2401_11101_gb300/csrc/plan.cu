@@ -102,8 +102,8 @@ int fft_elems(int n) { return (n % 3 == 0) ? 12 : 8; }
 
 bool fft_len_ok(int n) {
     if (n <= 0 || n > kMaxFft) return false;
-    if (is_pow2(n)) return n >= 8;
-    return n % 3 == 0 && is_pow2(n / 3) && n >= 12;
+    if (is_pow2(n)) return n >= 8 && n / 8 <= kMaxFftThreads;
+    return n % 3 == 0 && is_pow2(n / 3) && n >= 12 && n / 12 <= kMaxFftThreads;
 }
 
 int fft_size_at_least(double n) {
@@ -448,8 +448,8 @@ int lamino_plan(lamino_plan_t* out, int n0, int n1, int n2, int nproj, int det_w
         char buf[256];
         for (int n : lens)
             if (!fft_len_ok(n) && p->fourier_ok) {
-                snprintf(buf, sizeof buf, "FFT length %d of the Fourier form is not 2^k (>= 16) or "
-                         "3*2^k (>= 12) up to %d", n, kMaxFft);
+                snprintf(buf, sizeof buf, "FFT length %d of the Fourier form is not 2^k (8 .. 4096) "
+                         "or 3*2^k (12 .. 6144)", n);
                 p->fourier_why = buf;
                 p->fourier_ok = false;
             }

@@ -324,3 +324,28 @@ def test_explicit_nonuniform_angles(L):
     print(f"explicit angles: direct relL2 {ed:.2e}, fourier relL2 {ef:.2e}")
     assert ed <= 1e-5
     assert ef <= 1e-4
+
+
+def test_unsupported_sizes_fail_cleanly(L):
+    # more angles than the gridding kernel takes: the Fourier form reports
+    # EUNSUPPORTED, the plan and the direct form keep working
+    g = I.Geometry(16, 16, 8, 3200, 8, 24, math.radians(20.0))
+    q = torch.as_tensor(I.random_projections(g, 29), dtype=torch.float32).cuda()
+    with plan_for(L, g) as p:
+        with pytest.raises(L.LaminoError) as e:
+            p.backproject_fourier(q)
+        assert e.value.code == -5
+        v = p.backproject_direct(q)
+        p.status()
+        assert torch.isfinite(v).all()
+    # a 4096-wide volume needs 8192-point x1/x2 grids: more threads per FFT
+    # than a block of the FFT kernels holds, so the plan refuses the Fourier form
+    g = I.Geometry(4096, 4096, 2, 2, 2, 64, math.radians(20.0))
+    q = torch.as_tensor(I.random_projections(g, 30), dtype=torch.float32).cuda()
+    with plan_for(L, g) as p:
+        with pytest.raises(L.LaminoError) as e:
+            p.backproject_fourier(q)
+        assert e.value.code == -5 and "FFT length" in str(e.value)
+        v = p.backproject_direct(q)
+        p.status()
+        assert torch.isfinite(v).all()
