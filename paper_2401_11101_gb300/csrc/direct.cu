@@ -112,12 +112,10 @@ __global__ void __launch_bounds__(kThreads) k_direct(const __grid_constant__ CUt
         const double X0 = X0i - 0.5 * a.n0, Y0 = Y0i - 0.5 * a.n1, Z0 = Z0i - 0.5 * a.n2;
         const uint32_t bytes = (uint32_t)(sizeof(float) * a.bw * a.bh);
         int issued = 0;
-        bool ok = true;
         for (int k = 0; k < a.nproj; ++k) {
             const int s = k % S;
             if (k >= S && !mbar_wait(smem_addr(empty + s), ((k / S) & 1) ^ 1)) {
                 atomicExch(a.err, 1);
-                ok = false;
                 break;
             }
             const double ct = a.trig64[2 * k], st = a.trig64[2 * k + 1];
@@ -147,7 +145,6 @@ __global__ void __launch_bounds__(kThreads) k_direct(const __grid_constant__ CUt
         // drain: wait for the copies this thread issued last (bounded)
         for (int k = std::max(0, issued - S); k < issued; ++k)
             if (!mbar_wait(smem_addr(full + (k % S)), (k / S) & 1)) atomicExch(a.err, 2);
-        (void)ok;
         return;
     }
 
