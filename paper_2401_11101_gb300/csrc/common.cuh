@@ -245,13 +245,6 @@ struct SeqP {
     __device__ __forceinline__ void st(int i, float2 v) const { re[i] = v.x; im[i] = v.y; }
 };
 
-// One Stockham autosort stage of radix R on a sequence of length n held in
-// shared memory (the decimation-in-time autosort formulation, see e.g.
-// Govindaraju et al., SC 2008). Each of the t threads of the sequence stages
-// its E/R butterflies' inputs in registers, the block synchronises, and the
-// outputs are written back in place (the barrier separates all reads from all
-// writes). Butterfly j reads x[j + r n/R]; with k = j mod ns it twiddles by
-// exp(-+2 pi i k r/(ns R)), transforms and writes x[(j - k) R + k + r ns].
 // Barrier of the threads that share one FFT sequence: the whole block
 // (mode 0), the warp (mode 1: groups of at most 32 threads) or named barrier
 // 1 + gid over the group's T threads (mode 2). Every thread of the group
@@ -266,6 +259,14 @@ __device__ __forceinline__ void fft_sync(int mode, int gid, int T) {
     }
 }
 
+// One Stockham autosort stage of radix R on a sequence of length n held in
+// shared memory (the decimation-in-time autosort formulation, see e.g.
+// Govindaraju et al., SC 2008). Each of the t threads of the sequence stages
+// its E/R butterflies' inputs in registers, the threads of the sequence
+// synchronise (fft_sync), and the outputs are written back in place (the
+// barrier separates all reads from all writes). Butterfly j reads
+// x[j + r n/R]; with k = j mod ns it twiddles by exp(-+2 pi i k r/(ns R)),
+// transforms and writes x[(j - k) R + k + r ns].
 template <int E, int R, typename S>
 __device__ __forceinline__ void fft_stage(S x, const FftDesc& f, int tid, bool active, int ns,
                                           float s, int smode = 0, int gid = 0, int gT = 0) {

@@ -2,9 +2,10 @@
 // interpolation on the detector) and its exact transpose (the forward
 // operator of Eq. fwd in the same discretisation).
 //
-// Backprojector: one CTA owns a tile of TX x TY columns (x1, x2) and TZ
-// slices; each consumer thread keeps its column's TZ voxels in registers. For
-// every angle a producer warp stages the detector footprint of the tile
+// Backprojector: one CTA owns a tile of BX x BY columns (x1, x2) and BZ
+// slices; each consumer thread keeps the BZ voxels of its two columns in
+// registers as packed pairs. For every angle a producer warp stages the
+// detector footprint of the tile
 // (rows/columns the tile projects onto, zero outside the detector) into
 // shared memory with a TMA tiled copy; consumers wait on the stage's
 // mbarrier, sample bilinearly, and release the stage. Along x3 the detector

@@ -3,7 +3,8 @@
 //   colfft  : second pass of the 2D FFT of every projection (along detector
 //             rows v), keeping the k_v >= 0 half of the spectrum and writing
 //             it plane-major: G[l][k][m]. Real projections make the planes
-//             -l the conjugates of planes l (the x3 pass uses 2 Re).
+//             -l the conjugates of planes l (the x3 pass uses 2 Re). Also
+//             writes per-chunk bounds of the values for the gridding.
 //   grid    : per k_v plane l and band of T2 rows of the oversampled x2 grid,
 //             Gaussian spreading of every point (k, m) at the frequency of
 //             Eq. uneqspace onto a shared-memory band of the 2x oversampled
@@ -188,18 +189,20 @@ __device__ __forceinline__ int block_scan(int* v, int n, int* tmp) {
 // Gridding of one band of T2 rows of plane l, accumulated in fixed point.
 //
 // Shared-memory float atomics are emulated (about 5x slower than the native
-// int32 shared atomics), so the band accumulates integers: pass 1 bounds the
-// band by S1 = sum of max(|Re v|, |Im v|) and Smax = the largest such value
-// over its points; every tap is scaled by q = min(2^30/S1, 2^21/Smax), so no
-// single contribution reaches 2^22 (the range of the float-to-int rounding
-// below) and no cell sum can reach 2^31 (a cell never holds more than all the
-// band's points). The rounding error is at most 1/2 per tap, about 1e-9 of S1.
-// Taps are rounded to integers with one FMA against 1.5*2^23 (the integer then
-// sits in the low mantissa bits) instead of a float-to-int conversion.
+// int32 shared atomics), so the band accumulates integers. S1 >= the sum of
+// max(|Re v|, |Im v|) over the band's points and Smax >= the largest such
+// value come from the column FFT's chunk statistics (every chunk of C columns
+// that holds a point of a line interval); every tap is scaled by
+// q = min(2^30/S1, 2^21/Smax), so no single contribution reaches 2^22 (the
+// range of the float-to-int rounding below) and no cell sum can reach 2^31 (a
+// cell never holds more than all the band's points). The rounding error is at
+// most 1/2 per tap. Taps are rounded to integers with one FMA against
+// 1.5*2^23 (the integer then sits in the low mantissa bits) instead of a
+// float-to-int conversion.
 //
 // The band's points (every line's m-intervals) are numbered through a block
-// prefix sum and dealt to all threads evenly; each thread loops only over the
-// rows of its point that fall inside the band.
+// prefix sum; each warp takes 32 consecutive points, and each thread loops
+// only over the rows of its point that fall inside the band.
 constexpr float kRoundMagic = 12582912.0f;   // 1.5 * 2^23
 constexpr int kRoundMagicBits = 0x4B400000;  // its bit pattern
 
@@ -373,7 +376,7 @@ __global__ void __launch_bounds__(1024, 1) k_grid(GridArgs a) {
     S1 *= 1.01f;
     const float q = (S1 > 0.f) ? fminf(1073741824.0f / S1, 2097152.0f / Smax) : 1.0f;
 
-    // pass 2: spread
+    // spread
     const uint32_t s_re = (uint32_t)__cvta_generic_to_shared(Ui_re);
     const uint32_t plane_bytes = 4u * (uint32_t)(T2 * ld);
     for (int base = warp * 32; base < total; base += nwarps * 32) {
