@@ -36,7 +36,7 @@ class Request:
     tilt: float
     arrival: float                 # seconds after the start of the run
     d: object = None               # projections (host tensor, ideally pinned)
-    form: str = "fourier"
+    form: str = "fourier"          # "fourier", "direct", or "auto" (Fourier if it fits the budget)
     kind: str = "shepp"
 
     @property
@@ -97,6 +97,8 @@ class Server:
         self.backend = backend
         self.slots = slots
         self.budget = budget_bytes if budget_bytes is not None else backend.default_budget()
+        if hasattr(backend, "budget"):
+            backend.budget = self.budget      # lets "auto" requests choose a form that fits
         self.timeout_s = timeout_s
         self.poll_s = poll_s
         self.clock = clock
@@ -178,7 +180,11 @@ class Server:
 
 
 class CudaBackend:
-    """Runs requests with liblamino on one GPU, one CUDA stream per slot."""
+    """Runs requests with liblamino on one GPU, one CUDA stream per slot.
+
+    A request with form "auto" runs the Fourier form when its HBM footprint
+    fits the server's budget and falls back to the direct form (projections,
+    filtered rows and volume only) when it does not."""
 
     def __init__(self, device: int = 0, slots: int = 4, keep_volumes: bool = True):
         import torch
@@ -188,6 +194,7 @@ class CudaBackend:
         self.streams = [torch.cuda.Stream(device=self.device) for _ in range(slots)]
         self.idle = collections.OrderedDict()     # key -> [Plan] (LRU order)
         self.keep_volumes = keep_volumes
+        self.budget = None                         # set by the Server
         self._ws = {}
 
     def default_budget(self) -> int:
@@ -203,15 +210,27 @@ class CudaBackend:
         with self.torch.cuda.device(self.device):
             return self.L.Plan(r.n0, r.n1, r.n2, r.nproj, r.det_w, r.det_h, r.tilt)
 
-    def footprint(self, r: Request) -> int:
-        if r.key not in self._ws:
+    def _form_bytes(self, r: Request, form: str) -> int:
+        key = (r.key, form)
+        if key not in self._ws:
             with self.torch.cuda.device(self.device):
                 p = self._plan(r)
-                ws = p.workspace_bytes(r.form)
+                ws = p.workspace_bytes(form)
                 self.idle.setdefault(r.key, []).append(p)
             esz = 2 if r.d is None else r.d.element_size()
-            self._ws[r.key] = ws + r.nproj * r.det_h * r.det_w * (esz + 4) + 4 * r.nvox
-        return self._ws[r.key]
+            self._ws[key] = ws + r.nproj * r.det_h * r.det_w * (esz + 4) + 4 * r.nvox
+        return self._ws[key]
+
+    def form_of(self, r: Request) -> str:
+        """The form a request runs in ("auto": Fourier unless it exceeds the budget)."""
+        if r.form != "auto":
+            return r.form
+        if self.budget is None or self._form_bytes(r, "fourier") <= self.budget:
+            return "fourier"
+        return "direct"
+
+    def footprint(self, r: Request) -> int:
+        return self._form_bytes(r, self.form_of(r))
 
     def evict(self, target_free: int):
         # drop idle plans (tables + workspaces) least recently used first
@@ -231,7 +250,7 @@ class CudaBackend:
         with torch.cuda.device(self.device), torch.cuda.stream(s):
             d = r.d.to(self.device, non_blocking=True)
             vol = torch.empty(p.shape_vol, dtype=torch.float32, device=self.device)
-            p.fbp(d, form=r.form, kind=r.kind, out=vol)
+            p.fbp(d, form=self.form_of(r), kind=r.kind, out=vol)
             host = None
             if self.keep_volumes:
                 host = torch.empty(p.shape_vol, dtype=torch.float32, pin_memory=True)

@@ -142,3 +142,26 @@ def test_results_same_alone_and_in_the_mix():
             alone = p.fbp(r.d.cuda(), form=r.form, kind=r.kind).cpu()
         err = float((o.volume - alone).norm() / alone.norm())
         assert err <= 1e-6, (r.rid, err)
+
+
+@pytest.mark.gpu
+def test_auto_form_falls_back_to_direct_when_short_of_memory():
+    from paper_2401_11101_gb300 import _build, inputs as I, lamino as L
+    _build.build()
+    be = S.CudaBackend(0, slots=1)
+    r = S.Request(0, 64, 64, 32, 48, 96, 32, 0.35, 0.0)
+    g = I.Geometry(r.n0, r.n1, r.n2, r.nproj, r.det_h, r.det_w, r.tilt)
+    r.d = I.project_boxed(I.ellipsoid_params(g, 8, seed=70), g, device="cuda").half().cpu().pin_memory()
+    r.form = "auto"
+    direct = be._form_bytes(r, "direct")
+    fourier = be._form_bytes(r, "fourier")
+    assert direct < fourier
+    # a budget between the two footprints: admitted, in the direct form
+    rep = S.Server(be, slots=1, budget_bytes=(direct + fourier) // 2).run([r])
+    assert rep.outcomes[0].status == "ok" and be.form_of(r) == "direct"
+    with L.Plan(r.n0, r.n1, r.n2, r.nproj, r.det_w, r.det_h, r.tilt) as p:
+        alone = p.fbp(r.d.cuda(), form="direct", kind=r.kind).cpu()
+    assert float((rep.outcomes[0].volume - alone).norm() / alone.norm()) <= 1e-6
+    # with room for both, the same request runs in the Fourier form
+    be.budget = fourier * 2
+    assert be.form_of(r) == "fourier"
