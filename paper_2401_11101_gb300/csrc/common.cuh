@@ -344,11 +344,199 @@ __device__ __forceinline__ void fft_run(float2* x, const FftDesc& f, int tid, bo
     fft_run<E>(SeqC{x}, f, tid, active, s);
 }
 
+// v * exp(s i a) for the angle a with cosine c and sine sn.
+__device__ __forceinline__ float2 ctw(float2 v, float c, float sn, float s) {
+    const float y = s * sn;
+    return make_float2(v.x * c - v.y * y, v.x * y + v.y * c);
+}
+
+// DFT of length 16 in registers, exponent sign s, as 4 x 4: with n = 4a + b
+// and k = c + 4d, X[c + 4d] = sum_b w4^(bd) w16^(bc) sum_a v[4a + b] w4^(ac),
+// w_m = exp(s 2 pi i / m).
+__device__ __forceinline__ void dft16(float2* v, float s) {
+    const float c1 = 0.92387953251128675613f;   // cos(pi/8)
+    const float c3 = 0.38268343236508977173f;   // cos(3pi/8)
+    const float r = 0.70710678118654752440f;    // cos(pi/4)
+    float2 A[4][4];
+#pragma unroll
+    for (int b = 0; b < 4; ++b) {
+        float2 u[4] = {v[b], v[4 + b], v[8 + b], v[12 + b]};
+        bfly<4>(u, s);
+#pragma unroll
+        for (int c = 0; c < 4; ++c) A[b][c] = u[c];
+    }
+    // w16^(bc): angles pi bc / 8 for bc = 1, 2, 3, 4, 6, 9
+    A[1][1] = ctw(A[1][1], c1, c3, s);
+    A[1][2] = ctw(A[1][2], r, r, s);
+    A[1][3] = ctw(A[1][3], c3, c1, s);
+    A[2][1] = ctw(A[2][1], r, r, s);
+    A[2][2] = cmul_si(A[2][2], s);
+    A[2][3] = ctw(A[2][3], -r, r, s);
+    A[3][1] = ctw(A[3][1], c3, c1, s);
+    A[3][2] = ctw(A[3][2], -r, r, s);
+    A[3][3] = ctw(A[3][3], -c1, -c3, s);
+#pragma unroll
+    for (int c = 0; c < 4; ++c) {
+        float2 u[4] = {A[0][c], A[1][c], A[2][c], A[3][c]};
+        bfly<4>(u, s);
+#pragma unroll
+        for (int d = 0; d < 4; ++d) v[c + 4 * d] = u[d];
+    }
+}
+
+// v[c] *= w^(u c) for c = 1..15, w = exp(s 2 pi i / n), from the table
+// tw[j] = exp(-2 pi i j / n) (12 u < n): w^(u c) = tw[4 q u] tw[u]^r for
+// c = 4q + r, four table loads and at most two products per twiddle (fewer
+// live registers than fifteen loads).
+__device__ __forceinline__ void twiddle16(float2* v, const float2* __restrict__ tw, int u, float s) {
+    const float sg = (s > 0.f) ? -1.f : 1.f;
+    float2 w1 = __ldg(tw + u);
+    w1.y *= sg;
+    const float2 w2 = cmul(w1, w1), w3 = cmul(w2, w1);
+    v[1] = cmul(v[1], w1);
+    v[2] = cmul(v[2], w2);
+    v[3] = cmul(v[3], w3);
+#pragma unroll
+    for (int q = 1; q < 4; ++q) {
+        float2 wq = __ldg(tw + 4 * q * u);
+        wq.y *= sg;
+        v[4 * q] = cmul(v[4 * q], wq);
+        v[4 * q + 1] = cmul(v[4 * q + 1], cmul(wq, w1));
+        v[4 * q + 2] = cmul(v[4 * q + 2], cmul(wq, w2));
+        v[4 * q + 3] = cmul(v[4 * q + 3], cmul(wq, w3));
+    }
+}
+
+// 512-point FFT of the sequence x (shared memory, natural order in and out,
+// unnormalised, exponent sign s) by the 32 lanes of one warp: the four-step
+// split 512 = 16 x 32. With n = 32a + t and k = c + 16e,
+//   X[c + 16e] = sum_t w32^(te) [w512^(tc) sum_a x[32a + t] w16^(ac)].
+// Lane t takes the inner 16-point DFT of column t and its twiddles; after one
+// transpose through x itself, lane (c, p) = (lane / 2, lane % 2) takes the
+// 16-point DFT over the samples t = 2m + p of row c, and a radix-2 exchange
+// between the two lanes of a pair (shuffles) completes the 32-point DFT over t:
+// X[c + 16e + 256p] = E[e] + (-1)^p w32^e O[e]. Two shared-memory round trips
+// instead of one per radix-8 stage, and only warp barriers. The transpose
+// rotates row c by 2c slots so that its row writes and its column reads both
+// take the minimum two wavefronts. tw: exp(-2 pi i u / 512), u in [0, 512).
+__device__ __forceinline__ void fft512_warp(float2* x, const float2* __restrict__ tw, float s, int lane) {
+    float2 v[16];
+#pragma unroll
+    for (int a = 0; a < 16; ++a) v[a] = x[32 * a + lane];
+    dft16(v, s);
+    twiddle16(v, tw, lane, s);
+    __syncwarp();
+#pragma unroll
+    for (int c = 0; c < 16; ++c) x[32 * c + ((lane + 2 * c) & 31)] = v[c];
+    __syncwarp();
+    const int c = lane >> 1, p = lane & 1;
+#pragma unroll
+    for (int m = 0; m < 16; ++m) v[m] = x[32 * c + ((2 * m + p + 2 * c) & 31)];
+    dft16(v, s);
+    // odd lanes: w32^e, cos and sin of pi e / 16
+    const float a1 = 0.98078528040323044913f, a3 = 0.83146961230254523708f;
+    const float a5 = 0.55557023301960222474f, a7 = 0.19509032201612826785f;
+    const float c1 = 0.92387953251128675613f, c3 = 0.38268343236508977173f;
+    const float r = 0.70710678118654752440f;
+    if (p) {
+        v[1] = ctw(v[1], a1, a7, s);
+        v[2] = ctw(v[2], c1, c3, s);
+        v[3] = ctw(v[3], a3, a5, s);
+        v[4] = ctw(v[4], r, r, s);
+        v[5] = ctw(v[5], a5, a3, s);
+        v[6] = ctw(v[6], c3, c1, s);
+        v[7] = ctw(v[7], a7, a1, s);
+        v[8] = cmul_si(v[8], s);
+        v[9] = ctw(v[9], -a7, a1, s);
+        v[10] = ctw(v[10], -c3, c1, s);
+        v[11] = ctw(v[11], -a5, a3, s);
+        v[12] = ctw(v[12], -r, r, s);
+        v[13] = ctw(v[13], -a3, a5, s);
+        v[14] = ctw(v[14], -c1, c3, s);
+        v[15] = ctw(v[15], -a1, a7, s);
+    }
+    __syncwarp();
+#pragma unroll
+    for (int e = 0; e < 16; ++e) {
+        float2 o;
+        o.x = __shfl_xor_sync(0xffffffffu, v[e].x, 1);
+        o.y = __shfl_xor_sync(0xffffffffu, v[e].y, 1);
+        x[c + 16 * e + 256 * p] = p ? csub(o, v[e]) : cadd(v[e], o);
+    }
+}
+
+// 1024-point FFT of the sequence x (as fft512_warp) by the 64 threads of one
+// pair of warps, tid in [0, 64), synchronised on named barrier bar (64
+// threads): 1024 = 16 x 64. With n = 64a + t and k = c + 16e,
+//   X[c + 16e] = sum_t w64^(te) [w1024^(tc) sum_a x[64a + t] w16^(ac)].
+// Thread t takes the inner 16-point DFT of column t and its twiddles; after a
+// transpose through x (row c rotated by 4c slots), thread (c, r) = (tid / 4,
+// tid % 4) takes the 16-point DFT D_r over the samples t = 4m + r of row c and
+// its twiddles w64^(re); the radix-4 DFT over r between the four lanes of a
+// quad (two shuffle butterflies) gives X[c + 16e + 256q] = sum_r w4^(rq)
+// w64^(re) D_r[e], lane r producing q = 2 (r % 2) + r / 2.
+__device__ __forceinline__ void fft1024_pair(float2* x, const float2* __restrict__ tw, float s, int tid,
+                                             int bar) {
+    float2 v[16];
+#pragma unroll
+    for (int a = 0; a < 16; ++a) v[a] = x[64 * a + tid];
+    dft16(v, s);
+    twiddle16(v, tw, tid, s);
+    fft_sync(2, bar - 1, 64);
+#pragma unroll
+    for (int c = 0; c < 16; ++c) x[64 * c + ((tid + 4 * c) & 63)] = v[c];
+    fft_sync(2, bar - 1, 64);
+    const int c = tid >> 2, r = tid & 3;
+#pragma unroll
+    for (int m = 0; m < 16; ++m) v[m] = x[64 * c + ((4 * m + r + 4 * c) & 63)];
+    dft16(v, s);
+    twiddle16(v, tw, 16 * r, s);
+    const int b1 = r >> 1, b0 = r & 1;
+#pragma unroll
+    for (int e = 0; e < 16; ++e) {
+        // butterfly over r and r ^ 2; lane 3 then takes the w4 factor
+        float2 o;
+        o.x = __shfl_xor_sync(0xffffffffu, v[e].x, 2);
+        o.y = __shfl_xor_sync(0xffffffffu, v[e].y, 2);
+        float2 a = b1 ? csub(o, v[e]) : cadd(v[e], o);
+        if (b1 & b0) a = cmul_si(a, s);
+        v[e] = a;
+    }
+    fft_sync(2, bar - 1, 64);   // every read of x precedes the writes below
+    const int q = 2 * b0 + b1;
+#pragma unroll
+    for (int e = 0; e < 16; ++e) {
+        float2 o;
+        o.x = __shfl_xor_sync(0xffffffffu, v[e].x, 1);
+        o.y = __shfl_xor_sync(0xffffffffu, v[e].y, 1);
+        x[c + 16 * e + 256 * q] = b0 ? csub(o, v[e]) : cadd(v[e], o);
+    }
+}
+
 // FFTs of nseq sequences at base + i*ld with every thread of the block: groups
-// of blockDim/f.t sequences run side by side (blockDim must be >= f.t).
-// Ends with a block-wide barrier.
+// of blockDim/f.t sequences run side by side (blockDim must be >= f.t). Length
+// 512 goes one sequence per warp (fft512_warp) when blockDim is whole warps,
+// length 1024 one per pair of warps (fft1024_pair) when blockDim is whole
+// pairs and at most 15 of them (named barriers 1..15). Ends with a block-wide
+// barrier.
 template <int E>
 __device__ __forceinline__ void fft_many(float2* base, int ld, int nseq, const FftDesc& f, float s) {
+    if constexpr (E == 8) {
+        if (f.n == 512 && (blockDim.x & 31) == 0) {
+            const int lane = threadIdx.x & 31;
+            for (int seq = threadIdx.x >> 5; seq < nseq; seq += blockDim.x >> 5)
+                fft512_warp(base + (size_t)seq * ld, f.tw, s, lane);
+            __syncthreads();
+            return;
+        }
+        if (f.n == 1024 && (blockDim.x & 63) == 0 && blockDim.x <= 15 * 64) {
+            const int g = threadIdx.x >> 6, tid = threadIdx.x & 63;
+            for (int seq = g; seq < nseq; seq += blockDim.x >> 6)
+                fft1024_pair(base + (size_t)seq * ld, f.tw, s, tid, g + 1);
+            __syncthreads();
+            return;
+        }
+    }
     const int T = f.t;
     const int par = blockDim.x / T;
     if (par == 0) return;   // a sequence needs more threads than the block has (the plan refuses this)

@@ -40,6 +40,7 @@ def plan_for(L, g, **kw):
     I.Geometry(8, 8, 8, 8, 8, 12, math.radians(20.0)),
     I.Geometry(16, 24, 8, 9, 11, 23, math.radians(25.0)),
     I.Geometry(16, 16, 8, 12, 10, 26, 0.0),
+    I.Geometry(16, 16, 256, 4, 400, 24, math.radians(20.0)),  # Hf = M3 = 512: one warp per FFT
 ])
 def test_fourier_projector_matches_oracle(L, geom):
     mu = I.random_volume(geom, 31).astype(np.float32)
@@ -60,6 +61,20 @@ def test_adjoint_identity_gpu(L, form):
         lhs = float(torch.dot(p.project(mu, form).double().ravel(), q.double().ravel())) * math.pi / g.nproj
         rhs = float(torch.dot(mu.double().ravel(), p.backproject(q, form).double().ravel()))
     print(f"adjoint {form}: lhs {lhs:.8e} rhs {rhs:.8e} rel {abs(lhs - rhs) / abs(rhs):.2e}")
+    assert abs(lhs - rhs) <= 2e-5 * abs(rhs)
+
+
+@pytest.mark.parametrize("geom", [
+    I.Geometry(8, 400, 8, 3, 150, 420, math.radians(20.0)),   # M2 = 1024 (x2 pass), Wf = 512
+    I.Geometry(8, 8, 512, 4, 800, 12, math.radians(20.0)),    # Hf = M3 = 1024
+])
+def test_fourier_adjoint_identity_long_transforms(L, geom):
+    mu = torch.as_tensor(I.random_volume(geom, 35), dtype=torch.float32).cuda()
+    q = torch.as_tensor(I.random_projections(geom, 36), dtype=torch.float32).cuda()
+    with plan_for(L, geom) as p:
+        lhs = float(torch.dot(p.project(mu, "fourier").double().ravel(), q.double().ravel())) * math.pi / geom.nproj
+        rhs = float(torch.dot(mu.double().ravel(), p.backproject(q, "fourier").double().ravel()))
+    print(f"adjoint fourier {geom}: rel {abs(lhs - rhs) / abs(rhs):.2e}")
     assert abs(lhs - rhs) <= 2e-5 * abs(rhs)
 
 

@@ -171,6 +171,9 @@ def test_fourier_parity_c1(L):
     I.Geometry(32, 32, 16, 7, 24, 46, math.radians(-20.0)),   # negative tilt, odd nproj
     I.Geometry(16, 16, 16, 1, 16, 24, math.radians(40.0)),    # one angle
     I.Geometry(16, 24, 8, 9, 11, 23, math.radians(25.0)),     # odd detector sizes
+    I.Geometry(16, 16, 256, 4, 400, 24, math.radians(20.0)),  # Hf = M3 = 512: one warp per FFT
+    I.Geometry(16, 16, 512, 4, 800, 24, math.radians(20.0)),  # Hf = M3 = 1024: a warp pair per FFT
+    I.Geometry(8, 400, 8, 3, 150, 420, math.radians(20.0)),   # M2 = 1024, Wf = 512
 ])
 def test_fourier_parity_edge_cases(L, geom):
     q = I.random_projections(geom, 26).astype(np.float32)
