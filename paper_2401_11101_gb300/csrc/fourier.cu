@@ -549,6 +549,14 @@ void set_smem(K kern, size_t smem) {
     cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
 }
 
+// Threads of a block that transforms C sequences with fft_many: a warp per
+// 512-point sequence, a pair of warps per 1024-point one (the register-resident
+// paths), else f.t per sequence; 128 to 512.
+int fft_block_threads(const FftDesc& f, int C) {
+    const int per = (f.e == 8 && f.n == 512) ? 32 : (f.e == 8 && f.n == 1024) ? 64 : f.t;
+    return std::min(512, std::max(128, C * per));
+}
+
 
 // ============================================================================
 // Transpose of the Fourier-form backprojection (the forward operator of
@@ -823,7 +831,7 @@ int launch_colfft(lamino_plan_t p, int k0, int k1, cudaStream_t s) {
         const int C = CH;
         size_t smem = (size_t)C * (f.n + 1) * sizeof(float2);
         dim3 grid(p->Wf / C, k1 - k0);
-        int threads = std::min(512, std::max(C * f.t, 128));
+        int threads = fft_block_threads(f, C);
         ProfScope prof(p, "colfft", s);
         if (f.e == 8) {
             set_smem(k_colfft<8>, smem);
@@ -891,7 +899,7 @@ int launch_colifft(lamino_plan_t p, cudaStream_t s) {
         while (C > 1 && (size_t)C * (f.n + 1) * sizeof(float2) > 72 * 1024) C /= 2;
         size_t smem = (size_t)C * (f.n + 1) * sizeof(float2);
         dim3 grid((p->n0 + C - 1) / C, p->L);
-        int threads = std::min(512, std::max(128, C * f.t));
+        int threads = fft_block_threads(f, C);
         ProfScope prof(p, "colifft", s);
         if (f.e == 8) {
             set_smem(k_colifft<8>, smem);
@@ -917,7 +925,7 @@ int launch_zusfft(lamino_plan_t p, float* vol, int i10, int i11, cudaStream_t s)
         while (C > 1 && bytes(C) > 72 * 1024) C /= 2;
         size_t smem = bytes(C);
         dim3 grid((p->n0 + C - 1) / C, i11 - i10);
-        int threads = std::min(512, std::max(128, C * f.t));
+        int threads = fft_block_threads(f, C);
         ProfScope prof(p, "zusfft", s);
         if (f.e == 8) {
             set_smem(k_zusfft<8>, smem);
@@ -953,7 +961,7 @@ int launch_project_fourier(lamino_plan_t p, const float* vol, float* d, cudaStre
         while (C > 1 && (size_t)C * (f.n + 1) * sizeof(float2) > 72 * 1024) C /= 2;
         size_t smem = (size_t)C * (f.n + 1) * sizeof(float2);
         dim3 grid((p->n0 + C - 1) / C, p->n1);
-        int threads = std::min(512, std::max(128, C * f.t));
+        int threads = fft_block_threads(f, C);
         ProfScope prof(p, "zusfft_t", s);
         if (f.e == 8) {
             set_smem(k_zusfft_t<8>, smem);
@@ -970,7 +978,7 @@ int launch_project_fourier(lamino_plan_t p, const float* vol, float* d, cudaStre
         while (C > 1 && (size_t)C * (f.n + 1) * sizeof(float2) > 72 * 1024) C /= 2;
         size_t smem = (size_t)C * (f.n + 1) * sizeof(float2);
         dim3 grid((p->n0 + C - 1) / C, p->L);
-        int threads = std::min(512, std::max(128, C * f.t));
+        int threads = fft_block_threads(f, C);
         ProfScope prof(p, "colifft_t", s);
         if (f.e == 8) {
             set_smem(k_colifft_t<8>, smem);
@@ -1024,7 +1032,7 @@ int launch_project_fourier(lamino_plan_t p, const float* vol, float* d, cudaStre
         while (C > 1 && (size_t)C * (f.n + 1) * sizeof(float2) > 100 * 1024) C /= 2;
         size_t smem = (size_t)C * (f.n + 1) * sizeof(float2);
         dim3 grid(p->Wf / C, p->nproj);
-        int threads = std::min(512, std::max(C * f.t, 128));
+        int threads = fft_block_threads(f, C);
         ProfScope prof(p, "colfft_t", s);
         if (f.e == 8) {
             set_smem(k_colfft_t<8>, smem);
