@@ -97,19 +97,37 @@ def _stream(device) -> int:
     return torch.cuda.current_stream(device).cuda_stream
 
 
+def _form(form: str) -> int:
+    if form not in FORMS:
+        raise ValueError(f"form must be one of {sorted(FORMS)}, not {form!r}")
+    return FORMS[form]
+
+
+def _filter(kind: str) -> int:
+    if kind not in FILTERS:
+        raise ValueError(f"filter kind must be one of {sorted(FILTERS)}, not {kind!r}")
+    return FILTERS[kind]
+
+
 class Plan:
     """A reconstruction plan for one geometry (owns device tables/workspaces)."""
 
     def __init__(self, n0, n1, n2, nproj, det_w, det_h, tilt, angles=None, usfft_w=0,
                  usfft_wz=0, wf=0, hf=0, grid_rows=0, device=None):
-        self._lib = load_library()
-        self.device = torch.device("cuda", torch.cuda.current_device() if device is None
-                                   else torch.device(device).index or 0)
         self._h = ctypes.c_void_p()
+        ang_list = None
+        if angles is not None:
+            ang_list = [float(a) for a in angles]
+            if len(ang_list) != nproj:
+                # a shorter list would otherwise reach the library zero-padded
+                raise ValueError(f"angles has {len(ang_list)} entries, nproj is {nproj}")
+        self._lib = load_library()
+        idx = None if device is None else torch.device(device).index
+        self.device = torch.device("cuda", torch.cuda.current_device() if idx is None else idx)
         opts = _Opts(usfft_w, usfft_wz, wf, hf, grid_rows)
         ang = None
-        if angles is not None:
-            arr = (ctypes.c_double * nproj)(*[float(a) for a in angles])
+        if ang_list is not None:
+            arr = (ctypes.c_double * nproj)(*ang_list)
             ang = ctypes.cast(arr, ctypes.POINTER(ctypes.c_double))
         with torch.cuda.device(self.device):
             rc = self._lib.lamino_plan(ctypes.byref(self._h), n0, n1, n2, nproj, det_w, det_h,
@@ -151,7 +169,7 @@ class Plan:
         d = self._tensor(d, self.shape_proj, tuple(DTYPES), "d")
         q = self._out(out, self.shape_proj)
         self._check(self._lib.lamino_filter(self._h, d.data_ptr(), DTYPES[d.dtype], q.data_ptr(),
-                                            FILTERS[kind], _stream(self.device)))
+                                            _filter(kind), _stream(self.device)))
         return q
 
     def backproject_direct(self, q, out=None):
@@ -179,13 +197,14 @@ class Plan:
         return v
 
     def backproject(self, q, form="fourier", out=None):
+        _form(form)
         return (self.backproject_fourier if form == "fourier" else self.backproject_direct)(q, out)
 
     def fbp(self, d, form="fourier", kind="shepp", out=None):
         d = self._tensor(d, self.shape_proj, tuple(DTYPES), "d")
         v = self._out(out, self.shape_vol)
-        self._check(self._lib.lamino_fbp(self._h, FORMS[form], d.data_ptr(), DTYPES[d.dtype],
-                                         v.data_ptr(), FILTERS[kind], _stream(self.device)))
+        self._check(self._lib.lamino_fbp(self._h, _form(form), d.data_ptr(), DTYPES[d.dtype],
+                                         v.data_ptr(), _filter(kind), _stream(self.device)))
         return v
 
     def fbp_host(self, d_host, out_host, form="fourier", kind="shepp"):
@@ -197,21 +216,21 @@ class Plan:
             raise ValueError("fbp_host: shape mismatch")
         if out_host.dtype != torch.float32 or d_host.dtype not in DTYPES:
             raise ValueError("fbp_host: dtype mismatch")
-        self._check(self._lib.lamino_fbp_host(self._h, FORMS[form], d_host.data_ptr(),
+        self._check(self._lib.lamino_fbp_host(self._h, _form(form), d_host.data_ptr(),
                                               DTYPES[d_host.dtype], out_host.data_ptr(),
-                                              FILTERS[kind], _stream(self.device)))
+                                              _filter(kind), _stream(self.device)))
         return out_host
 
     def project(self, vol, form="direct", out=None):
         vol = self._tensor(vol, self.shape_vol, (torch.float32,), "vol")
         d = self._out(out, self.shape_proj)
-        self._check(self._lib.lamino_project(self._h, FORMS[form], vol.data_ptr(), d.data_ptr(),
+        self._check(self._lib.lamino_project(self._h, _form(form), vol.data_ptr(), d.data_ptr(),
                                              _stream(self.device)))
         return d
 
     def workspace_bytes(self, form="fourier") -> int:
         b = ctypes.c_size_t()
-        self._check(self._lib.lamino_workspace_bytes(self._h, FORMS[form], ctypes.byref(b)))
+        self._check(self._lib.lamino_workspace_bytes(self._h, _form(form), ctypes.byref(b)))
         return int(b.value)
 
     def profile(self, enable: bool = True):

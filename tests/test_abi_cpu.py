@@ -77,3 +77,22 @@ def test_plan_without_gpu_reports_cuda_error(lib):
         pytest.skip("a GPU is present")
     rc, msg = _plan(lib, 64, 64, 64, 64, 96, 64, 0.35)
     assert rc == L.ECUDA and "device" in msg
+
+
+def test_binding_rejects_wrong_angle_count():
+    # checked before the library or the device is touched: a shorter list
+    # would otherwise reach lamino_plan zero-padded
+    with pytest.raises(ValueError, match="angles"):
+        L.Plan(8, 8, 8, 4, 12, 8, 0.3, angles=[0.0, 1.0, 2.0])
+    with pytest.raises(ValueError, match="angles"):
+        L.Plan(8, 8, 8, 2, 12, 8, 0.3, angles=[0.0, 1.0, 2.0])
+
+
+@pytest.mark.parametrize("bad", ["Fourier", "auto", "fft", ""])
+def test_binding_rejects_unknown_form_and_filter(bad):
+    with pytest.raises(ValueError, match="form"):
+        L._form(bad)
+    with pytest.raises(ValueError, match="filter"):
+        L._filter(bad)
+    assert L._form("direct") == L.DIRECT and L._form("fourier") == L.FOURIER
+    assert L._filter("parzen") == L.PARZEN
