@@ -196,12 +196,28 @@ class CudaBackend:
         self.keep_volumes = keep_volumes
         self.budget = None                         # set by the Server
         self._ws = {}
+        self.draining = []                         # handles released before their work finished
 
     def default_budget(self) -> int:
         free, total = self.torch.cuda.mem_get_info(self.device)
         return int(0.8 * free)
 
+    def _to_idle(self, key, plan):
+        self.idle.setdefault(key, []).append(plan)
+        self.idle.move_to_end(key)
+
+    def _drain(self):
+        # plans of timed-out requests rejoin the pool once their work has finished
+        still = []
+        for h in self.draining:
+            if h["ev"].query():
+                self._to_idle(h["req"].key, h["plan"])
+            else:
+                still.append(h)
+        self.draining = still
+
     def _plan(self, r: Request):
+        self._drain()
         lst = self.idle.get(r.key)
         if lst:
             p = lst.pop()
@@ -211,13 +227,13 @@ class CudaBackend:
             return self.L.Plan(r.n0, r.n1, r.n2, r.nproj, r.det_w, r.det_h, r.tilt)
 
     def _form_bytes(self, r: Request, form: str) -> int:
-        key = (r.key, form)
+        esz = 2 if r.d is None else r.d.element_size()
+        key = (r.key, form, esz)
         if key not in self._ws:
             with self.torch.cuda.device(self.device):
                 p = self._plan(r)
                 ws = p.workspace_bytes(form)
                 self.idle.setdefault(r.key, []).append(p)
-            esz = 2 if r.d is None else r.d.element_size()
             self._ws[key] = ws + r.nproj * r.det_h * r.det_w * (esz + 4) + 4 * r.nvox
         return self._ws[key]
 
@@ -267,11 +283,14 @@ class CudaBackend:
         return h["host"]
 
     def release(self, h):
-        r = h["req"]
         h["d"].record_stream(h["stream"])
         h["vol"].record_stream(h["stream"])
-        self.idle.setdefault(r.key, []).append(h["plan"])
-        self.idle.move_to_end(r.key)
+        if not h["ev"].query():
+            # a timed-out request: its kernels may still use the plan's
+            # workspaces, so the plan stays out of the pool until they finish
+            self.draining.append(h)
+            return
+        self._to_idle(h["req"].key, h["plan"])
 
 
 def poisson_arrivals(n: int, rate: float, seed: int) -> np.ndarray:

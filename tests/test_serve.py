@@ -97,6 +97,39 @@ def test_oversize_request_rejected_and_timeout_reported():
     assert be.concurrent == 0
 
 
+def test_timed_out_plan_rejoins_the_pool_only_after_its_work_finishes():
+    # CudaBackend.release without a GPU: events and tensors are stand-ins
+    import collections
+
+    class Ev:
+        def __init__(self):
+            self.done = False
+
+        def query(self):
+            return self.done
+
+    class Buf:
+        def record_stream(self, s):
+            pass
+
+    b = S.CudaBackend.__new__(S.CudaBackend)
+    b.idle, b.draining = collections.OrderedDict(), []
+    r = S.Request(0, 8, 8, 8, 4, 12, 8, 0.3, 0.0)
+    ev, plan = Ev(), object()
+    b.release({"req": r, "plan": plan, "ev": ev, "d": Buf(), "vol": Buf(), "host": None, "stream": None})
+    assert r.key not in b.idle and len(b.draining) == 1
+    b._drain()
+    assert r.key not in b.idle
+    ev.done = True
+    b._drain()
+    assert b.idle[r.key] == [plan] and not b.draining
+    ev2 = Ev()
+    ev2.done = True
+    plan2 = object()
+    b.release({"req": r, "plan": plan2, "ev": ev2, "d": Buf(), "vol": Buf(), "host": None, "stream": None})
+    assert b.idle[r.key] == [plan, plan2]
+
+
 def test_arrivals_are_honoured():
     clk = FakeClock()
     be = FakeBackend(sizes=[1] * 4, durations=[1] * 4)
