@@ -30,6 +30,15 @@ int orc_num_threads(void) {
 #endif
 }
 
+/* Threads of the OpenMP loops from now on (timing of the CPU baseline). */
+void orc_set_num_threads(int n) {
+#ifdef _OPENMP
+    if (n > 0) omp_set_num_threads(n);
+#else
+    (void)n;
+#endif
+}
+
 /* Detector value with zero outside [0,W) x [0,H). */
 static double tap(const double* q, int H, int W, long r, long j) {
     if (r < 0 || r >= H || j < 0 || j >= W) return 0.0;
@@ -244,4 +253,67 @@ void orc_fourier_adjoint_coeffs(const double* vol, int n0, int n1, int n2, int n
                 Aim[o] = si;
             }
         }
+}
+
+/* Periodic interpolation kernel of period N with the Nyquist term dropped:
+ *   K_N(t) = (1/N) sum_{m=-N/2+1}^{N/2-1} exp(2 pi i m t / N)
+ *          = sin(pi (N-1) t / N) / (N sin(pi t / N)),
+ * a real, even, N-periodic function equal to (N-1)/N at multiples of N. */
+static double periodic_kernel(double t, int N) {
+    double tr = t - N * floor(t / N + 0.5);   /* reduce to [-N/2, N/2) */
+    double s = sin(ORC_PI * tr / N);
+    if (fabs(tr) < 1e-9) return (double)(N - 1) / N;
+    return sin(ORC_PI * (N - 1) * tr / N) / (N * s);
+}
+
+/*
+ * The Fourier form by its spatial reading. Substituting the 2D DFT of the
+ * zero-padded projection into the type-1 sum of Eq. fftadj (Eq. uneqspace grid)
+ * and summing the geometric series over m and l gives
+ *   vol(x) = (pi/Ntheta) sum_k sum_{r,j} q_k(r, j) K_Wf(a_k.x + W/2 - j) K_Hf(b_k.x + H/2 - r):
+ * direct backprojection with the periodic (trigonometric) interpolation
+ * kernel of the padded detector in place of the bilinear one. The padding
+ * offsets cancel; Wf and Hf enter only as the kernel periods. This route needs
+ * no spectra, so it scales to paper-size projections; it and
+ * orc_bp_fourier_columns are two independent evaluations of one sum.
+ *
+ * q holds nq projections at angles theta[0..nq); `weight` is the quadrature
+ * weight per angle (pi/Ntheta of the full angle set). Columns cols[c] =
+ * (i0, i1); out[c][n2] is overwritten.
+ */
+void orc_bp_trig_columns(const double* q, int nq, int H, int W, const double* theta, double phi,
+                         int Wf, int Hf, int n0, int n1, int n2, const int* cols, int ncol,
+                         double weight, double* out) {
+    double sp = sin(phi), cp = cos(phi);
+    double* rows = (double*)malloc(sizeof(double) * (size_t)nq * H);   /* per angle: rows at u */
+    for (long c = 0; c < ncol; ++c) {
+        double x1 = cols[2 * c] - 0.5 * n0, x2 = cols[2 * c + 1] - 0.5 * n1;
+        /* interpolate every detector row of every projection at u = a_k.x */
+#pragma omp parallel for schedule(dynamic)
+        for (long k = 0; k < nq; ++k) {
+            double ct = cos(theta[k]), st = sin(theta[k]);
+            double u = x1 * ct + x2 * st + 0.5 * W;
+            double* kr = (double*)malloc(sizeof(double) * W);
+            for (int j = 0; j < W; ++j) kr[j] = periodic_kernel(u - j, Wf);
+            const double* qk = q + (size_t)k * H * W;
+            for (int r = 0; r < H; ++r) {
+                double acc = 0.0;
+                for (int j = 0; j < W; ++j) acc += qk[(size_t)r * W + j] * kr[j];
+                rows[(size_t)k * H + r] = acc;
+            }
+            free(kr);
+        }
+        /* then along the detector column at v = b_k.x for every slice */
+#pragma omp parallel for schedule(dynamic)
+        for (long i2 = 0; i2 < n2; ++i2) {
+            double x3 = i2 - 0.5 * n2, acc = 0.0;
+            for (long k = 0; k < nq; ++k) {
+                double ct = cos(theta[k]), st = sin(theta[k]);
+                double v = x1 * st * sp - x2 * ct * sp + x3 * cp + 0.5 * H;
+                for (int r = 0; r < H; ++r) acc += rows[(size_t)k * H + r] * periodic_kernel(v - r, Hf);
+            }
+            out[c * n2 + i2] = acc * weight;
+        }
+    }
+    free(rows);
 }

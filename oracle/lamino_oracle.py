@@ -40,6 +40,7 @@ import math
 import os
 
 import numpy as np
+from scipy import fft as _sfft
 
 from . import build as _build
 
@@ -55,6 +56,7 @@ def _load():
         I = ctypes.POINTER(ctypes.c_int)
         c_int, c_double = ctypes.c_int, ctypes.c_double
         lib.orc_num_threads.restype = c_int
+        lib.orc_set_num_threads.argtypes = [c_int]
         lib.orc_bp_direct.argtypes = [D, c_int, c_int, c_int, D, c_double, c_int, c_int,
                                       c_int, c_int, c_int, D]
         lib.orc_bp_direct_columns.argtypes = [D, c_int, c_int, c_int, D, c_double, c_int,
@@ -65,6 +67,8 @@ def _load():
                                                c_double, D]
         lib.orc_bp_fourier_full4.argtypes = [D, D, c_int, c_int, c_int, c_double, c_double, D,
                                              c_double, c_int, c_int, c_int, c_double, D]
+        lib.orc_bp_trig_columns.argtypes = [D, c_int, c_int, c_int, D, c_double, c_int, c_int,
+                                            c_int, c_int, c_int, I, c_int, c_double, D]
         lib.orc_fourier_adjoint_coeffs.argtypes = [D, c_int, c_int, c_int, c_int, c_int, c_int,
                                                    c_double, c_double, D, c_double, D, D]
         _lib = lib
@@ -82,6 +86,16 @@ def _ip(a: np.ndarray):
 def num_threads() -> int:
     """OpenMP threads the C loops use."""
     return int(_load().orc_num_threads())
+
+
+def set_num_threads(n: int) -> None:
+    """Threads of the C loops and of the row filter's FFTs from now on."""
+    global _workers
+    _load().orc_set_num_threads(int(n))
+    _workers = int(n)
+
+
+_workers = os.cpu_count() or 1
 
 
 def _f64(a) -> np.ndarray:
@@ -155,13 +169,20 @@ def filter_response(Wp: int, tilt: float, kind: str) -> np.ndarray:
 
 
 def filter_rows(d, geom, kind: str = "ramp") -> np.ndarray:
-    """Apply W along detector rows: pad to Wp, DFT, x H(f), inverse DFT, crop."""
+    """Apply W along detector rows: pad to Wp, DFT, x H(f), inverse DFT, crop.
+
+    The rows are real and H(f) is real and even, so the half spectrum of a
+    real-input FFT (scipy.fft on all host threads; the Nyquist bin at
+    f = +1/2 carries H(1/2) = H(-1/2)) gives the same filtered rows."""
     d = _f64(d)
     W = d.shape[-1]
     Wp = padded_sizes(geom)["Wp"]
-    Hf = filter_response(Wp, geom.tilt, kind)
-    spec = np.fft.fft(d, n=Wp, axis=-1)
-    return np.ascontiguousarray(np.real(np.fft.ifft(spec * Hf, axis=-1))[..., :W])
+    Hf = filter_response(Wp, geom.tilt, kind)[: Wp // 2 + 1]
+    Hf[-1] = filter_response(Wp, geom.tilt, kind)[Wp // 2]
+    workers = _workers
+    spec = _sfft.rfft(d, n=Wp, axis=-1, workers=workers)
+    spec *= Hf
+    return np.ascontiguousarray(_sfft.irfft(spec, n=Wp, axis=-1, workers=workers)[..., :W])
 
 
 # ----------------------------------------------------------------------------
@@ -248,6 +269,25 @@ def backproject_fourier_columns(q, geom, cols, angle_index=None) -> np.ndarray:
                                    _dp(_theta(geom, angle_index)), float(geom.tilt), geom.n0,
                                    geom.n1, geom.n2, _ip(cols), cols.shape[0],
                                    _fourier_scale(geom, Wf, Hf), _dp(out))
+    return out
+
+
+def backproject_trig_columns(q, geom, cols, angle_index=None) -> np.ndarray:
+    """The same sum as backproject_fourier_columns, evaluated in detector space:
+    (pi/Ntheta) sum_k sum_{r,j} q_k(r, j) K_Wf(a_k.x + W/2 - j) K_Hf(b_k.x + H/2 - r)
+    with the periodic kernel K_N(t) = (1/N) sum over |m| < N/2 of exp(2 pi i m t/N)
+    (the geometric series of the type-1 sum of Eq. fftadj over the Nyquist-free
+    frequencies, summed in closed form). Needs no padded spectra, so it serves
+    paper-size projections; angle_index as for backproject_direct_columns.
+    Columns cols[c] = (i0, i1); returns [ncol, n2]."""
+    q = _f64(q)
+    Wf, Hf, _, _, _, _ = _fourier_frame(geom)
+    cols = np.ascontiguousarray(cols, dtype=np.int32)
+    out = np.zeros((cols.shape[0], geom.n2))
+    _load().orc_bp_trig_columns(_dp(q), q.shape[0], geom.det_h, geom.det_w,
+                                _dp(_theta(geom, angle_index)), float(geom.tilt), Wf, Hf,
+                                geom.n0, geom.n1, geom.n2, _ip(cols), cols.shape[0],
+                                math.pi / geom.nproj, _dp(out))
     return out
 
 
