@@ -25,7 +25,8 @@
  *     call says otherwise; the plan owns its tables and workspaces;
  *   - calls are asynchronous on the given stream (0 = legacy default stream);
  *     outputs are valid once that stream has synchronised. One plan must not
- *     be used from two streams at the same time (its workspace is shared);
+ *     be used from two streams or two host threads at the same time (its
+ *     workspace and its settings are shared);
  *   - every call returns a status (LAMINO_OK = 0 or a negative code below);
  *     lamino_last_error() gives a message for the last failure of a plan.
  */
@@ -68,11 +69,21 @@ typedef struct lamino_plan_s* lamino_plan_t;
 /* Optional plan parameters; pass NULL for the defaults. Zero fields take the
  * default as well. */
 typedef struct {
-    int usfft_w;     /* Gaussian half-width (grid cells) of the 2D gridding; default 4 */
-    int usfft_wz;    /* half-width of the 1D gridding along x3; default 6 */
+    int usfft_w;     /* Gaussian half-width (grid cells) of the 2D gridding; 0: the plan
+                        chooses the smallest w in [4, 8] whose predicted relative L2 error
+                        (usfft_err_est) is <= 0.9e-4: 4 for axes of >= 24 voxels, 5 for
+                        the smallest grids */
+    int usfft_wz;    /* half-width of the 1D gridding along x3; 0: chosen likewise (6) */
     int wf;          /* override of the padded Fourier detector width Wf */
     int hf;          /* override of the padded Fourier detector height Hf */
     int grid_rows;   /* rows of the oversampled grid per gridding CTA (power of two; tuning) */
+    int z_chunk;     /* z chunking (Sec. 5: the 2D USFFT of Eq. fftfwdsplit by chunks of
+                        slices, the 1D USFFT by chunks of columns, the direct form by
+                        chunks of x3 slices): k_v planes per chunk of the gridding and
+                        the x2 pass, and output slices per launch of the direct form
+                        (rounded up to its 16-slice tile); 0: no chunking. Chunking the
+                        Fourier form keeps only one chunk of x1-pass planes and shrinks
+                        its workspace (lamino_workspace_bytes); results are equal */
 } lamino_opts;
 
 /* Sizes a plan derived (all integers). */
@@ -83,6 +94,12 @@ typedef struct {
     int m1, m2, m3;  /* oversampled USFFT grids (>= 2*n0, 2*n1, 2*n2) */
     int usfft_w, usfft_wz;
     int planes;      /* k_v planes gridded (hf/2; the rest follow by Hermitian symmetry) */
+    float usfft_err_est;  /* predicted relative L2 error of the Fourier form against the
+                             exact sum, for evenly spread volume energy: truncation and
+                             aliasing of the Gaussian kernel after deconvolution, per
+                             axis, calibrated on random projections */
+    int z_chunk;     /* the plan's z_chunk (0: none) */
+    int plane_chunk; /* k_v planes per chunk of the Fourier form (planes when not chunked) */
 } lamino_plan_info;
 
 /*
@@ -140,8 +157,8 @@ int lamino_backproject_direct(lamino_plan_t plan, const float* q, float* vol,
  * r' = b_k.x + det_h/2 + (hf-det_h)/2. Evaluated with a 2D FFT per projection,
  * Gaussian gridding of the half spectrum onto each tilted k_v plane (2x
  * oversampled), inverse 2D FFT and deconvolution per plane, then a 1D USFFT
- * along x3. Accuracy is set by usfft_w / usfft_wz (relative L2 error about
- * 1e-5 at the defaults).
+ * along x3. Accuracy is set by usfft_w / usfft_wz (relative L2 error below
+ * 1e-4 at the widths the plan chooses; lamino_plan_info.usfft_err_est).
  *   q     : projections in `dtype`; vol : float32 [n2][n1][n0], overwritten.
  * Uses the plan's workspace (see lamino_workspace_bytes), allocated on the
  * first call. Errors: EINVAL, ENOMEM, ECUDA.
@@ -248,8 +265,21 @@ int lamino_profile(lamino_plan_t plan, int enable);
 int lamino_profile_read(lamino_plan_t plan, lamino_kernel_time* out, int max, int* n);
 
 /* Bytes of device workspace a form needs beyond the plan tables (admission
- * control by HBM footprint). */
+ * control by HBM footprint), under the plan's current z chunking. */
 int lamino_workspace_bytes(lamino_plan_t plan, int form, size_t* bytes);
+
+/* Device memory the plan holds right now: its tables plus every workspace it
+ * has allocated so far (admission control of a server that keeps idle plans
+ * resident). */
+int lamino_device_bytes(lamino_plan_t plan, size_t* bytes);
+
+/*
+ * lamino_set_z_chunk -- change the z chunking of a plan (see lamino_opts.z_chunk;
+ * Sec. 5, chunking by slices and columns). Frees the plan's Fourier workspaces
+ * (which waits for the device); the next call allocates them for the new
+ * layout. Results do not depend on the chunking. Errors: EINVAL (z_chunk < 0).
+ */
+int lamino_set_z_chunk(lamino_plan_t plan, int z_chunk);
 
 /* Message of the last failure of `plan` (or of the last failed lamino_plan
  * call when plan is NULL). The pointer stays valid until the next call. */

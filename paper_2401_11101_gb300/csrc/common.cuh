@@ -53,8 +53,11 @@ struct lamino_plan_s {
 
     // derived sizes
     int Wp = 0, Wf = 0, Hf = 0, L = 0, M1 = 0, M2 = 0, M3 = 0;
-    int w = 5, wz = 6, offu = 0, offv = 0;
+    int w = 4, wz = 6, offu = 0, offv = 0;
+    double err_est = 0.0;                // predicted USFFT relL2 error (usfft_err_est)
     int grid_rows = 0;                   // band height of the gridding kernel (0: default)
+    int z_chunk = 0;                     // k_v planes per F3-F5 chunk and output slices per
+                                         // direct launch (0: no chunking)
     double t1 = 0, t2 = 0, t3 = 0;       // Gaussian widths (grid cells^2) per axis
     lam::FftDesc fWp, fWf, fHf, fM1, fM2, fM3;
     int zmax = 0;                        // taps per cell of the x3 gridding table
@@ -74,6 +77,7 @@ struct lamino_plan_s {
     int2* d_ztap = nullptr;        // [L][2 wz] (cell, weight bits) per plane: the same taps by plane
     float2* d_tw = nullptr;        // all FFT twiddle tables
     int* d_err = nullptr;          // device error word (bounded waits)
+    size_t table_bytes = 0;        // device bytes of the tables above
 
     // workspaces (owned, allocated on first use)
     void* ws_a = nullptr; size_t ws_a_bytes = 0;   // row spectra R / gridded planes V
@@ -141,20 +145,39 @@ int launch_filter(lamino_plan_t p, const void* d, int dtype, float* q, int kind,
 int validate_dtype_kind(lamino_plan_t p, int dtype, int kind);
 int launch_rowfft(lamino_plan_t p, const void* d, int dtype, float2* R, int kind /* -1: no filter */,
                   cudaStream_t s, long row0 = 0, long row1 = -1);
+// Views of the Fourier form's two workspaces A and B (fourier_bufs). R, the
+// row spectra, and G, the plane-major half spectra (followed by the column
+// FFT's chunk statistics st), are whole; V holds the x1-pass planes of one
+// chunk of zc planes and P the deconvolved planes of all L planes.
+//   zc == L (no z chunking): A = R, then V [L][n0][M2]; B = G + st, then P.
+//   zc <  L: A = R, then P [L][n1][n0] followed by V [zc][n0][M2]; B = G + st
+//            (G must outlive every plane chunk).
+// The transpose (lamino_project) uses the same views in reverse order.
+struct FourierBufs {
+    float2 *R, *G, *st, *V, *P;
+    int CH;    // columns per column-FFT block = statistics chunk
+    int zc;    // planes per chunk (F3-F5)
+};
+int fourier_workspace(lamino_plan_t p, size_t* a_bytes, size_t* b_bytes);
+FourierBufs fourier_bufs(lamino_plan_t p, void* a, void* b);
+int colfft_chunk(lamino_plan_t p);
+int plane_chunk(lamino_plan_t p);    // zc: planes per F3-F5 chunk (L when not chunked)
+
 // The Fourier form after the row pass, stage by stage: column FFT of the
-// projections [k0, k1), gridding + x1 inverse FFT, x2 inverse FFT, and the x3
-// USFFT of the x2 rows [i10, i11) of the volume. run_fourier_after_rows runs
-// them all in order.
-int launch_colfft(lamino_plan_t p, int k0, int k1, cudaStream_t s);
-int launch_grid(lamino_plan_t p, cudaStream_t s);
-int launch_colifft(lamino_plan_t p, cudaStream_t s);
-int launch_zusfft(lamino_plan_t p, float* vol, int i10, int i11, cudaStream_t s);
-int run_fourier_after_rows(lamino_plan_t p, float* vol, cudaStream_t s);
+// projections [k0, k1), gridding + x1 inverse FFT of the planes [l0, l1) into
+// V, x2 inverse FFT of those planes from V into P, and the x3 USFFT of the x2
+// rows [i10, i11) of the volume. run_fourier_after_rows runs them all, plane
+// chunk by plane chunk (F3-F5) and column chunk by column chunk (F6).
+int launch_colfft(lamino_plan_t p, const FourierBufs& fb, int k0, int k1, cudaStream_t s);
+int launch_grid(lamino_plan_t p, const FourierBufs& fb, int l0, int l1, cudaStream_t s);
+int launch_colifft(lamino_plan_t p, const FourierBufs& fb, int l0, int l1, cudaStream_t s);
+int launch_zusfft(lamino_plan_t p, const FourierBufs& fb, float* vol, int i10, int i11, cudaStream_t s);
+int run_planes(lamino_plan_t p, const FourierBufs& fb, cudaStream_t s);   // F3-F5, all chunks
+int run_fourier_after_rows(lamino_plan_t p, const FourierBufs& fb, float* vol, cudaStream_t s);
 int launch_direct(lamino_plan_t p, const float* q, float* vol, cudaStream_t s);
 int launch_project_direct(lamino_plan_t p, const float* vol, float* d, cudaStream_t s);
-int launch_project_fourier(lamino_plan_t p, const float* vol, float* d, cudaStream_t s);
-int fourier_workspace(lamino_plan_t p, size_t* a_bytes, size_t* b_bytes);
-int colfft_chunk(lamino_plan_t p);   // columns per column-FFT block = statistics chunk
+int launch_project_fourier(lamino_plan_t p, const FourierBufs& fb, const float* vol, float* d,
+                           cudaStream_t s);
 
 // device helpers --------------------------------------------------------------
 __device__ __forceinline__ float2 cmul(float2 a, float2 b) {

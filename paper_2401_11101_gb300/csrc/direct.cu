@@ -73,6 +73,7 @@ struct DirectArgs {
     float* vol;
     int* err;
     int nproj, n0, n1, n2, W, H;
+    int z0;                // first slice of the launch (z chunking); blockIdx.z counts tiles from it
     int bw, bh, stages, stage_floats;
     double sp, cp;
     float cpf, scale;
@@ -106,7 +107,7 @@ __global__ void __launch_bounds__(kThreads) k_direct(const __grid_constant__ CUt
     }
     __syncthreads();
 
-    const int X0i = blockIdx.x * BX, Y0i = blockIdx.y * BY, Z0i = blockIdx.z * BZ;
+    const int X0i = blockIdx.x * BX, Y0i = blockIdx.y * BY, Z0i = a.z0 + blockIdx.z * BZ;
     if (threadIdx.x >= kConsumers) {
         // ---------------- producer warp (lane 0 issues) ----------------
         if (threadIdx.x != kConsumers) return;
@@ -312,6 +313,7 @@ DirectArgs make_args(lamino_plan_t p, const DirectCfg& cfg) {
     a.vol = nullptr;
     a.err = p->d_err;
     a.nproj = p->nproj; a.n0 = p->n0; a.n1 = p->n1; a.n2 = p->n2; a.W = p->W; a.H = p->H;
+    a.z0 = 0;
     a.bw = cfg.bw; a.bh = cfg.bh; a.stages = cfg.stages;
     a.stage_floats = (a.bw * a.bh + 31) / 32 * 32;   // 128-byte aligned stages
     a.sp = sin(p->tilt);
@@ -352,11 +354,19 @@ int launch_direct(lamino_plan_t p, const float* q, float* vol, cudaStream_t s) {
     a.vol = vol;
     size_t smem = sizeof(float) * ((size_t)a.stages * a.stage_floats + (size_t)(BZ + 2) * a.bw) +
                   sizeof(StageMeta) * a.stages + 2 * sizeof(uint64_t) * a.stages;
-    dim3 grid((p->n0 + BX - 1) / BX, (p->n1 + BY - 1) / BY, (p->n2 + BZ - 1) / BZ);
     cudaFuncSetAttribute(k_direct, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    ProfScope prof(p, "direct", s);
-    k_direct<<<grid, kThreads, smem, s>>>(map, a);
-    LAM_LAUNCH_CHECK(p, "direct backprojection kernel");
+    // z chunking: one launch per slab of zs output slices (a multiple of the
+    // tile depth, so that the slabs' tiles never overlap); the last slab's
+    // tiles stop at n2 inside the kernel
+    const int zs = p->z_chunk > 0 ? (p->z_chunk + BZ - 1) / BZ * BZ : (p->n2 + BZ - 1) / BZ * BZ;
+    for (int z0 = 0; z0 < p->n2; z0 += zs) {
+        a.z0 = z0;
+        const int nz = std::min(zs, p->n2 - z0);
+        dim3 grid((p->n0 + BX - 1) / BX, (p->n1 + BY - 1) / BY, (nz + BZ - 1) / BZ);
+        ProfScope prof(p, "direct", s);
+        k_direct<<<grid, kThreads, smem, s>>>(map, a);
+        LAM_LAUNCH_CHECK(p, "direct backprojection kernel");
+    }
     return LAMINO_OK;
 }
 

@@ -89,6 +89,8 @@ struct GridArgs {
     const float* dec1;
     int nproj, Wf, Hf, n0, M1, M2, T2, ld;   // ld: row pitch of the band accumulator
     int ch;                                  // column chunk of the statistics
+    int L, l0;                               // planes of the half spectrum; first plane of
+                                             // the launch (blockIdx.y = l - l0; V is [l - l0])
     int civ_cap;                             // entries of the group table (0: none)
     float sinphi, c1, c2;  // c = -1/(4t) per axis
     FftDesc f1;
@@ -341,7 +343,7 @@ __global__ void __launch_bounds__(1024, 1) k_grid(GridArgs a) {
     int* civ = lcnt + nproj;                // [civ_cap] group table of the band list
     __shared__ float red_s[32], red_m[32];
     __shared__ int scan_tmp[32];
-    const int band = blockIdx.x, l = blockIdx.y;
+    const int band = blockIdx.x, l = a.l0 + blockIdx.y;
     const int s20 = band * T2;
     int* Ui_re = reinterpret_cast<int*>(Ure);
     int* Ui_im = reinterpret_cast<int*>(Uim);
@@ -356,7 +358,7 @@ __global__ void __launch_bounds__(1024, 1) k_grid(GridArgs a) {
     float lsum = 0.f, lmax = 0.f;
     const int total = band_list(a.trig, nproj, a.Wf, M2, rho, (float)(s20 - W),
                                 (float)(s20 + T2 + W - 1), ioff, ikm, lcnt, scan_tmp, nintv,
-                                a.st + l, a.ch, gridDim.y, &lsum, &lmax, civ, a.civ_cap);
+                                a.st + l, a.ch, a.L, &lsum, &lmax, civ, a.civ_cap);
     const int* civ_t = (total <= 32 * a.civ_cap) ? civ : nullptr;
     auto locate = [&](int base, int& k, int& m) -> bool {
         return band_locate(ioff, ikm, nintv, total, base, lane, k, m, civ_t);
@@ -453,7 +455,7 @@ __global__ void __launch_bounds__(1024, 1) k_grid(GridArgs a) {
         int s1 = i0 - n0 / 2;
         s1 += (s1 < 0) ? M1 : 0;
         const float dd = __ldg(a.dec1 + i0);
-        a.V[((size_t)l * n0 + i0) * M2 + s20 + rr] = make_float2(Ure[rr * ld + s1] * dd, Uim[rr * ld + s1] * dd);
+        a.V[((size_t)blockIdx.y * n0 + i0) * M2 + s20 + rr] = make_float2(Ure[rr * ld + s1] * dd, Uim[rr * ld + s1] * dd);
     }
 }
 
@@ -461,10 +463,10 @@ __global__ void __launch_bounds__(1024, 1) k_grid(GridArgs a) {
 template <int E>
 __global__ void __launch_bounds__(512, 2) k_colifft(const float2* __restrict__ V, float2* __restrict__ P,
                                                   int n0, int n1, FftDesc f2,
-                                                  const float* __restrict__ dec2, int C) {
+                                                  const float* __restrict__ dec2, int C, int l0) {
     extern __shared__ float2 sm[];
     const int M2 = f2.n, ld = M2 + 1;
-    const int l = blockIdx.y, i00 = blockIdx.x * C;
+    const int lv = blockIdx.y, l = l0 + lv, i00 = blockIdx.x * C;   // V holds planes [l0, ...)
     constexpr int U = 8;
     const int total = C * M2;
     for (int base = threadIdx.x; base < total; base += U * blockDim.x) {
@@ -473,7 +475,7 @@ __global__ void __launch_bounds__(512, 2) k_colifft(const float2* __restrict__ V
         for (int u = 0; u < U; ++u) {
             const int idx = base + u * blockDim.x;
             const int i0 = i00 + idx / M2;
-            v[u] = (idx < total && i0 < n0) ? V[((size_t)l * n0 + i0) * M2 + idx % M2] : make_float2(0.f, 0.f);
+            v[u] = (idx < total && i0 < n0) ? V[((size_t)lv * n0 + i0) * M2 + idx % M2] : make_float2(0.f, 0.f);
         }
 #pragma unroll
         for (int u = 0; u < U; ++u) {
@@ -604,10 +606,10 @@ __global__ void __launch_bounds__(512, 2) k_zusfft_t(const float* __restrict__ v
 template <int E>
 __global__ void __launch_bounds__(512, 2) k_colifft_t(const float2* __restrict__ Pt, float2* __restrict__ Vt,
                                                       int n0, int n1, FftDesc f2,
-                                                      const float* __restrict__ dec2, int C) {
+                                                      const float* __restrict__ dec2, int C, int l0) {
     extern __shared__ float2 sm[];
     const int M2 = f2.n, ld = M2 + 1;
-    const int l = blockIdx.y, i00 = blockIdx.x * C;
+    const int lv = blockIdx.y, l = l0 + lv, i00 = blockIdx.x * C;   // Vt holds planes [l0, ...)
     for (int i = threadIdx.x; i < C * ld; i += blockDim.x) sm[i] = make_float2(0.f, 0.f);
     __syncthreads();
     for (int idx = threadIdx.x; idx < C * n1; idx += blockDim.x) {
@@ -621,7 +623,7 @@ __global__ void __launch_bounds__(512, 2) k_colifft_t(const float2* __restrict__
     fft_many<E>(sm, ld, C, f2, -1.f);
     for (int idx = threadIdx.x; idx < C * M2; idx += blockDim.x) {
         const int c = idx / M2, s = idx % M2, i0 = i00 + c;
-        if (i0 < n0) Vt[((size_t)l * n0 + i0) * M2 + s] = sm[c * ld + s];
+        if (i0 < n0) Vt[((size_t)lv * n0 + i0) * M2 + s] = sm[c * ld + s];
     }
 }
 
@@ -640,7 +642,7 @@ __global__ void __launch_bounds__(512, 1) k_grid_t(GridArgs a, const float2* __r
     int* ikm = ioff + 4 * nproj + 1;
     int* lcnt = ikm + 4 * nproj;
     __shared__ int scan_tmp[32];
-    const int band = blockIdx.x, l = blockIdx.y, s20 = band * T2;
+    const int band = blockIdx.x, l = a.l0 + blockIdx.y, s20 = band * T2;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
     const int half = a.Wf / 2;
     for (int i = threadIdx.x; i < NR * ld; i += blockDim.x) X[i] = make_float2(0.f, 0.f);
@@ -651,7 +653,7 @@ __global__ void __launch_bounds__(512, 1) k_grid_t(GridArgs a, const float2* __r
         s2 -= (s2 >= M2) ? M2 : 0;
         int s1 = i0 - n0 / 2;
         s1 += (s1 < 0) ? M1 : 0;
-        X[rr * ld + s1] = cscale(Vt[((size_t)l * n0 + i0) * M2 + s2], __ldg(a.dec1 + i0));
+        X[rr * ld + s1] = cscale(Vt[((size_t)blockIdx.y * n0 + i0) * M2 + s2], __ldg(a.dec1 + i0));
     }
     __syncthreads();
     fft_many<E>(X, ld, NR, a.f1, -1.f);
@@ -802,159 +804,204 @@ int colfft_chunk(lamino_plan_t p) {
     return C;
 }
 
-// Workspace views of the Fourier form: row spectra R and, after the
-// gridding, the x1 pass V share workspace A; half spectra G (+ the chunk
-// statistics after them) and, after the x2 pass, the planes P share B.
-struct FourierBufs {
-    float2 *R, *G, *st, *V, *P;
-    int CH;
-};
-static FourierBufs fourier_bufs(lamino_plan_t p) {
-    FourierBufs b;
-    b.R = (float2*)p->ws_a;    // [nproj][H][Wf]
-    b.G = (float2*)p->ws_b;    // [L][nproj][Wf]
-    b.V = (float2*)p->ws_a;    // [L][n0][M2]   (R is dead by then)
-    b.P = (float2*)p->ws_b;    // [L][n1][n0]   (G is dead by then)
-    b.CH = colfft_chunk(p);
-    b.st = b.G + (size_t)p->L * p->nproj * p->Wf;
-    return b;
+// Planes per F3-F5 chunk: the plan's z_chunk, or every plane (no chunking).
+int plane_chunk(lamino_plan_t p) {
+    return (p->z_chunk > 0 && p->z_chunk < p->L) ? p->z_chunk : p->L;
 }
 
-int launch_colfft(lamino_plan_t p, int k0, int k1, cudaStream_t s) {
+// Workspace sizes (bytes) of A and B for the layouts described at FourierBufs.
+int fourier_workspace(lamino_plan_t p, size_t* a_bytes, size_t* b_bytes) {
+    const int zc = plane_chunk(p);
+    size_t R = (size_t)p->nproj * p->H * p->Wf;    // row spectra
+    size_t G = (size_t)p->L * p->nproj * p->Wf;    // half spectra, plane-major
+    G += G / colfft_chunk(p);                      // + chunk statistics (sum, max)
+    size_t P = (size_t)p->L * p->n1 * p->n0;       // deconvolved planes
+    size_t V = (size_t)zc * p->n0 * p->M2;         // x1-pass planes of one chunk
+    if (zc >= p->L) {
+        *a_bytes = sizeof(float2) * std::max(R, V);
+        *b_bytes = sizeof(float2) * std::max(G, P);
+    } else {
+        *a_bytes = sizeof(float2) * std::max(R, P + V);
+        *b_bytes = sizeof(float2) * G;
+    }
+    return LAMINO_OK;
+}
+
+FourierBufs fourier_bufs(lamino_plan_t p, void* a, void* b) {
+    FourierBufs f;
+    f.CH = colfft_chunk(p);
+    f.zc = plane_chunk(p);
+    f.R = (float2*)a;                                        // [nproj][H][Wf]
+    f.G = (float2*)b;                                        // [L][nproj][Wf]
+    f.st = f.G + (size_t)p->L * p->nproj * p->Wf;           // [nproj][Wf/CH][L]
+    if (f.zc >= p->L) {
+        f.V = (float2*)a;                                    // [L][n0][M2]  (R is dead by then)
+        f.P = (float2*)b;                                    // [L][n1][n0]  (G is dead by then)
+    } else {
+        f.P = (float2*)a;                                    // [L][n1][n0]  (R is dead by then)
+        f.V = f.P + (size_t)p->L * p->n1 * p->n0;            // [zc][n0][M2]
+    }
+    return f;
+}
+
+int launch_colfft(lamino_plan_t p, const FourierBufs& fb, int k0, int k1, cudaStream_t s) {
     if (k1 <= k0) return LAMINO_OK;
-    const FourierBufs fb = fourier_bufs(p);
-    float2 *R = fb.R, *G = fb.G, *st = fb.st;
-    const int CH = fb.CH;
     // column FFT (+ chunk statistics for the gridding bound, after G in B)
-    {
-        const FftDesc& f = p->fHf;
-        const int C = CH;
-        size_t smem = (size_t)C * (f.n + 1) * sizeof(float2);
-        dim3 grid(p->Wf / C, k1 - k0);
-        int threads = fft_block_threads(f, C);
-        ProfScope prof(p, "colfft", s);
-        if (f.e == 8) {
-            set_smem(k_colfft<8>, smem);
-            k_colfft<8><<<grid, threads, smem, s>>>(R, G, st, k0, p->nproj, p->H, p->Wf, p->L, p->offv, f, p->d_phv, C);
-        } else {
-            set_smem(k_colfft<12>, smem);
-            k_colfft<12><<<grid, threads, smem, s>>>(R, G, st, k0, p->nproj, p->H, p->Wf, p->L, p->offv, f, p->d_phv, C);
-        }
-        LAM_LAUNCH_CHECK(p, "column FFT kernel");
+    const FftDesc& f = p->fHf;
+    const int C = fb.CH;
+    size_t smem = (size_t)C * (f.n + 1) * sizeof(float2);
+    dim3 grid(p->Wf / C, k1 - k0);
+    int threads = fft_block_threads(f, C);
+    ProfScope prof(p, "colfft", s);
+    if (f.e == 8) {
+        set_smem(k_colfft<8>, smem);
+        k_colfft<8><<<grid, threads, smem, s>>>(fb.R, fb.G, fb.st, k0, p->nproj, p->H, p->Wf, p->L, p->offv, f,
+                                                 p->d_phv, C);
+    } else {
+        set_smem(k_colfft<12>, smem);
+        k_colfft<12><<<grid, threads, smem, s>>>(fb.R, fb.G, fb.st, k0, p->nproj, p->H, p->Wf, p->L, p->offv, f,
+                                                  p->d_phv, C);
     }
+    LAM_LAUNCH_CHECK(p, "column FFT kernel");
     return LAMINO_OK;
 }
 
-int launch_grid(lamino_plan_t p, cudaStream_t s) {
-    const FourierBufs fb = fourier_bufs(p);
-    float2 *G = fb.G, *st = fb.st, *V = fb.V;
-    const int CH = fb.CH;
-    // gridding + x1 inverse FFT
-    {
-        GridArgs a;
-        a.G = G; a.V = V; a.trig = p->d_trig; a.dec1 = p->d_dec1;
-        a.st = st; a.ch = CH;
-        a.nproj = p->nproj; a.Wf = p->Wf; a.Hf = p->Hf; a.n0 = p->n0; a.M1 = p->M1; a.M2 = p->M2;
-        a.sinphi = (float)sin(p->tilt);
-        a.c1 = (float)(-1.0 / (4.0 * p->t1));
-        a.c2 = (float)(-1.0 / (4.0 * p->t2));
-        a.f1 = p->fM1;
-        // Row pitch = 5 (mod 32) words: lanes holding consecutive points of one
-        // line (steps of ~1.33 cells) then fall in different banks for all but
-        // a narrow wedge of line directions (a pitch of 1 mod 32 stacks every
-        // near-anti-diagonal line into one bank).
-        a.ld = p->M1 + ((5 - p->M1) % 32 + 32) % 32;
-        int T2 = p->grid_rows > 0 ? p->grid_rows : 16;
-        while (T2 > 1 && (size_t)T2 * a.ld * sizeof(float2) > 132 * 1024) T2 /= 2;
-        while (p->M2 % T2) T2 /= 2;
-        a.T2 = T2;
-        // band accumulator (planar) + compact interval list + per-line counts
-        if (p->nproj > 4 * 768 || p->Wf > 8192)
-            return fail(p, LAMINO_EUNSUPPORTED, "gridding supports up to 3072 angles and Wf <= 8192");
-        size_t smem = (size_t)T2 * a.ld * sizeof(float2) + sizeof(int) * (9 * (size_t)p->nproj + 1);
-        if (smem > 220 * 1024)
-            return fail(p, LAMINO_EUNSUPPORTED, "gridding tile of %zu bytes exceeds shared memory", smem);
-        // group table in what is left (bands with more points bisect instead)
-        a.civ_cap = (int)std::min<size_t>(16384, (224 * 1024 - smem) / sizeof(int));
-        smem += sizeof(int) * (size_t)a.civ_cap;
-        int threads = 1024;
-        dim3 grid(p->M2 / T2, p->L);
-        ProfScope prof(p, "grid", s);
-        if (p->fM1.e == 8) dispatch_grid_w<8>(p->w, a, grid, threads, smem, s);
-        else dispatch_grid_w<12>(p->w, a, grid, threads, smem, s);
-        LAM_LAUNCH_CHECK(p, "gridding kernel");
-    }
+// Arguments of the gridding kernel and of its transpose shared by both.
+static GridArgs grid_args(lamino_plan_t p) {
+    GridArgs a;
+    a.G = nullptr; a.V = nullptr; a.st = nullptr;
+    a.trig = p->d_trig; a.dec1 = p->d_dec1;
+    a.ch = 1; a.civ_cap = 0;
+    a.nproj = p->nproj; a.Wf = p->Wf; a.Hf = p->Hf; a.n0 = p->n0; a.M1 = p->M1; a.M2 = p->M2;
+    a.L = p->L; a.l0 = 0;
+    a.sinphi = (float)sin(p->tilt);
+    a.c1 = (float)(-1.0 / (4.0 * p->t1));
+    a.c2 = (float)(-1.0 / (4.0 * p->t2));
+    a.f1 = p->fM1;
+    return a;
+}
+
+int launch_grid(lamino_plan_t p, const FourierBufs& fb, int l0, int l1, cudaStream_t s) {
+    if (l1 <= l0) return LAMINO_OK;
+    // gridding + x1 inverse FFT of planes [l0, l1) into V
+    GridArgs a = grid_args(p);
+    a.G = fb.G; a.V = fb.V; a.st = fb.st; a.ch = fb.CH;
+    a.l0 = l0;
+    // Row pitch = 5 (mod 32) words: lanes holding consecutive points of one
+    // line (steps of ~1.33 cells) then fall in different banks for all but
+    // a narrow wedge of line directions (a pitch of 1 mod 32 stacks every
+    // near-anti-diagonal line into one bank).
+    a.ld = p->M1 + ((5 - p->M1) % 32 + 32) % 32;
+    int T2 = p->grid_rows > 0 ? p->grid_rows : 16;
+    while (T2 > 1 && (size_t)T2 * a.ld * sizeof(float2) > 132 * 1024) T2 /= 2;
+    while (p->M2 % T2) T2 /= 2;
+    a.T2 = T2;
+    // band accumulator (planar) + compact interval list + per-line counts
+    if (p->nproj > 4 * 768 || p->Wf > 8192)
+        return fail(p, LAMINO_EUNSUPPORTED, "gridding supports up to 3072 angles and Wf <= 8192");
+    size_t smem = (size_t)T2 * a.ld * sizeof(float2) + sizeof(int) * (9 * (size_t)p->nproj + 1);
+    if (smem > 220 * 1024)
+        return fail(p, LAMINO_EUNSUPPORTED, "gridding tile of %zu bytes exceeds shared memory", smem);
+    // group table in what is left (bands with more points bisect instead)
+    a.civ_cap = (int)std::min<size_t>(16384, (224 * 1024 - smem) / sizeof(int));
+    smem += sizeof(int) * (size_t)a.civ_cap;
+    int threads = 1024;
+    dim3 grid(p->M2 / T2, l1 - l0);
+    ProfScope prof(p, "grid", s);
+    if (p->fM1.e == 8) dispatch_grid_w<8>(p->w, a, grid, threads, smem, s);
+    else dispatch_grid_w<12>(p->w, a, grid, threads, smem, s);
+    LAM_LAUNCH_CHECK(p, "gridding kernel");
     return LAMINO_OK;
 }
 
-int launch_colifft(lamino_plan_t p, cudaStream_t s) {
-    const FourierBufs fb = fourier_bufs(p);
-    float2 *V = fb.V, *P = fb.P;
-    // x2 inverse FFT
-    {
-        const FftDesc& f = p->fM2;
-        // <= ~72 KB per block so that several blocks share an SM and one
-        // block's loads overlap another's FFT
-        int C = 16;
-        while (C > 1 && (size_t)C * (f.n + 1) * sizeof(float2) > 72 * 1024) C /= 2;
-        size_t smem = (size_t)C * (f.n + 1) * sizeof(float2);
-        dim3 grid((p->n0 + C - 1) / C, p->L);
-        int threads = fft_block_threads(f, C);
-        ProfScope prof(p, "colifft", s);
-        if (f.e == 8) {
-            set_smem(k_colifft<8>, smem);
-            k_colifft<8><<<grid, threads, smem, s>>>(V, P, p->n0, p->n1, f, p->d_dec2, C);
-        } else {
-            set_smem(k_colifft<12>, smem);
-            k_colifft<12><<<grid, threads, smem, s>>>(V, P, p->n0, p->n1, f, p->d_dec2, C);
-        }
-        LAM_LAUNCH_CHECK(p, "x2 inverse FFT kernel");
+// Columns per block of the x2 pass: <= ~72 KB per block so that several
+// blocks share an SM and one block's loads overlap another's FFT.
+static int x2_chunk(const FftDesc& f) {
+    int C = 16;
+    while (C > 1 && (size_t)C * (f.n + 1) * sizeof(float2) > 72 * 1024) C /= 2;
+    return C;
+}
+
+int launch_colifft(lamino_plan_t p, const FourierBufs& fb, int l0, int l1, cudaStream_t s) {
+    if (l1 <= l0) return LAMINO_OK;
+    // x2 inverse FFT of planes [l0, l1): V (chunk-relative) -> P (absolute)
+    const FftDesc& f = p->fM2;
+    const int C = x2_chunk(f);
+    size_t smem = (size_t)C * (f.n + 1) * sizeof(float2);
+    dim3 grid((p->n0 + C - 1) / C, l1 - l0);
+    int threads = fft_block_threads(f, C);
+    ProfScope prof(p, "colifft", s);
+    if (f.e == 8) {
+        set_smem(k_colifft<8>, smem);
+        k_colifft<8><<<grid, threads, smem, s>>>(fb.V, fb.P, p->n0, p->n1, f, p->d_dec2, C, l0);
+    } else {
+        set_smem(k_colifft<12>, smem);
+        k_colifft<12><<<grid, threads, smem, s>>>(fb.V, fb.P, p->n0, p->n1, f, p->d_dec2, C, l0);
     }
+    LAM_LAUNCH_CHECK(p, "x2 inverse FFT kernel");
     return LAMINO_OK;
 }
 
-int launch_zusfft(lamino_plan_t p, float* vol, int i10, int i11, cudaStream_t s) {
+int launch_zusfft(lamino_plan_t p, const FourierBufs& fb, float* vol, int i10, int i11, cudaStream_t s) {
     if (i11 <= i10) return LAMINO_OK;
-    const FourierBufs fb = fourier_bufs(p);
-    float2* P = fb.P;
-    // x3 USFFT
-    {
-        const FftDesc& f = p->fM3;
-        int C = 16;
-        auto bytes = [&](int c) { return (size_t)c * ((size_t)p->L + f.n + 1) * sizeof(float2); };
-        while (C > 1 && bytes(C) > 72 * 1024) C /= 2;
-        size_t smem = bytes(C);
-        dim3 grid((p->n0 + C - 1) / C, i11 - i10);
-        int threads = fft_block_threads(f, C);
-        ProfScope prof(p, "zusfft", s);
-        if (f.e == 8) {
-            set_smem(k_zusfft<8>, smem);
-            k_zusfft<8><<<grid, threads, smem, s>>>(P, vol, p->L, p->n0, p->n1, p->n2, f, p->d_zoff,
-                                                     p->d_zl, p->d_zw, p->d_dec3, C, i10);
-        } else {
-            set_smem(k_zusfft<12>, smem);
-            k_zusfft<12><<<grid, threads, smem, s>>>(P, vol, p->L, p->n0, p->n1, p->n2, f, p->d_zoff,
-                                                     p->d_zl, p->d_zw, p->d_dec3, C, i10);
-        }
-        LAM_LAUNCH_CHECK(p, "x3 USFFT kernel");
+    // x3 USFFT of the columns of x2 rows [i10, i11)
+    const FftDesc& f = p->fM3;
+    int C = 16;
+    auto bytes = [&](int c) { return (size_t)c * ((size_t)p->L + f.n + 1) * sizeof(float2); };
+    while (C > 1 && bytes(C) > 72 * 1024) C /= 2;
+    size_t smem = bytes(C);
+    dim3 grid((p->n0 + C - 1) / C, i11 - i10);
+    int threads = fft_block_threads(f, C);
+    ProfScope prof(p, "zusfft", s);
+    if (f.e == 8) {
+        set_smem(k_zusfft<8>, smem);
+        k_zusfft<8><<<grid, threads, smem, s>>>(fb.P, vol, p->L, p->n0, p->n1, p->n2, f, p->d_zoff,
+                                                 p->d_zl, p->d_zw, p->d_dec3, C, i10);
+    } else {
+        set_smem(k_zusfft<12>, smem);
+        k_zusfft<12><<<grid, threads, smem, s>>>(fb.P, vol, p->L, p->n0, p->n1, p->n2, f, p->d_zoff,
+                                                  p->d_zl, p->d_zw, p->d_dec3, C, i10);
+    }
+    LAM_LAUNCH_CHECK(p, "x3 USFFT kernel");
+    return LAMINO_OK;
+}
+
+// F3-F5 over chunks of zc k_v planes (the 2D USFFT of the split of
+// Eq. fftfwdsplit, chunked by slices as in Sec. 5).
+int run_planes(lamino_plan_t p, const FourierBufs& fb, cudaStream_t s) {
+    int rc;
+    for (int l0 = 0; l0 < p->L; l0 += fb.zc) {
+        const int l1 = std::min(p->L, l0 + fb.zc);
+        if ((rc = launch_grid(p, fb, l0, l1, s))) return rc;
+        if ((rc = launch_colifft(p, fb, l0, l1, s))) return rc;
     }
     return LAMINO_OK;
 }
 
-int run_fourier_after_rows(lamino_plan_t p, float* vol, cudaStream_t s) {
+int run_fourier_after_rows(lamino_plan_t p, const FourierBufs& fb, float* vol, cudaStream_t s) {
     int rc;
-    if ((rc = launch_colfft(p, 0, p->nproj, s))) return rc;
-    if ((rc = launch_grid(p, s))) return rc;
-    if ((rc = launch_colifft(p, s))) return rc;
-    return launch_zusfft(p, vol, 0, p->n1, s);
+    if ((rc = launch_colfft(p, fb, 0, p->nproj, s))) return rc;
+    if ((rc = run_planes(p, fb, s))) return rc;
+    // F6 by column chunks (x2 rows), as many chunks as plane chunks
+    const int nch = (p->L + fb.zc - 1) / fb.zc;
+    for (int c = 0; c < nch; ++c) {
+        const int i10 = (int)((long)p->n1 * c / nch), i11 = (int)((long)p->n1 * (c + 1) / nch);
+        if ((rc = launch_zusfft(p, fb, vol, i10, i11, s))) return rc;
+    }
+    return LAMINO_OK;
 }
 
 
-int launch_project_fourier(lamino_plan_t p, const float* vol, float* d, cudaStream_t s) {
-    float2* Pt = (float2*)p->ws_b;   // [L][n1][n0]
-    float2* Vt = (float2*)p->ws_a;   // [L][n0][M2]
-    float2* Gt = (float2*)p->ws_b;   // [L][nproj][Wf]  (Pt is dead by then)
-    float2* Rt = (float2*)p->ws_a;   // [nproj][H][Wf]  (Vt is dead by then)
+int launch_project_fourier(lamino_plan_t p, const FourierBufs& fb, const float* vol, float* d,
+                           cudaStream_t s) {
+    // the backprojection's views in reverse order: Pt = P, Vt = V (one plane
+    // chunk at a time), Gt = G, Rt = R (P and V are dead by then)
+    float2* Pt = fb.P;   // [L][n1][n0]
+    float2* Vt = fb.V;   // [zc][n0][M2]
+    float2* Gt = fb.G;   // [L][nproj][Wf]
+    float2* Rt = fb.R;   // [nproj][H][Wf]
+    if (p->nproj > 4 * 512 || p->Wf > 8192)
+        return fail(p, LAMINO_EUNSUPPORTED, "Fourier projector supports up to 2048 angles");
     {   // x3
         const FftDesc& f = p->fM3;
         int C = 16;
@@ -972,59 +1019,53 @@ int launch_project_fourier(lamino_plan_t p, const float* vol, float* d, cudaStre
         }
         LAM_LAUNCH_CHECK(p, "x3 USFFT transpose kernel");
     }
-    {   // x2
-        const FftDesc& f = p->fM2;
-        int C = 16;
-        while (C > 1 && (size_t)C * (f.n + 1) * sizeof(float2) > 72 * 1024) C /= 2;
-        size_t smem = (size_t)C * (f.n + 1) * sizeof(float2);
-        dim3 grid((p->n0 + C - 1) / C, p->L);
-        int threads = fft_block_threads(f, C);
-        ProfScope prof(p, "colifft_t", s);
-        if (f.e == 8) {
-            set_smem(k_colifft_t<8>, smem);
-            k_colifft_t<8><<<grid, threads, smem, s>>>(Pt, Vt, p->n0, p->n1, f, p->d_dec2, C);
-        } else {
-            set_smem(k_colifft_t<12>, smem);
-            k_colifft_t<12><<<grid, threads, smem, s>>>(Pt, Vt, p->n0, p->n1, f, p->d_dec2, C);
+    GridArgs a = grid_args(p);
+    a.ld = p->M1 + 1;
+    int T2 = 8;
+    while (T2 > 1 && (size_t)(T2 + 2 * p->w - 1) * a.ld * sizeof(float2) > 150 * 1024) T2 /= 2;
+    while (p->M2 % T2) T2 /= 2;
+    a.T2 = T2;
+    const size_t gsmem = (size_t)(T2 + 2 * p->w - 1) * a.ld * sizeof(float2) + sizeof(int) * (9 * (size_t)p->nproj + 1);
+    if (gsmem > 220 * 1024)
+        return fail(p, LAMINO_EUNSUPPORTED, "gridding transpose tile of %zu bytes exceeds shared memory", gsmem);
+    for (int l0 = 0; l0 < p->L; l0 += fb.zc) {
+        const int l1 = std::min(p->L, l0 + fb.zc);
+        {   // x2 of planes [l0, l1): Pt -> Vt (chunk-relative)
+            const FftDesc& f = p->fM2;
+            const int C = x2_chunk(f);
+            size_t smem = (size_t)C * (f.n + 1) * sizeof(float2);
+            dim3 grid((p->n0 + C - 1) / C, l1 - l0);
+            int threads = fft_block_threads(f, C);
+            ProfScope prof(p, "colifft_t", s);
+            if (f.e == 8) {
+                set_smem(k_colifft_t<8>, smem);
+                k_colifft_t<8><<<grid, threads, smem, s>>>(Pt, Vt, p->n0, p->n1, f, p->d_dec2, C, l0);
+            } else {
+                set_smem(k_colifft_t<12>, smem);
+                k_colifft_t<12><<<grid, threads, smem, s>>>(Pt, Vt, p->n0, p->n1, f, p->d_dec2, C, l0);
+            }
+            LAM_LAUNCH_CHECK(p, "x2 FFT transpose kernel");
         }
-        LAM_LAUNCH_CHECK(p, "x2 FFT transpose kernel");
-    }
-    {   // gridding transpose
-        GridArgs a;
-        a.G = nullptr; a.V = nullptr; a.trig = p->d_trig; a.dec1 = p->d_dec1;
-        a.st = nullptr; a.ch = 1; a.civ_cap = 0;
-        a.nproj = p->nproj; a.Wf = p->Wf; a.Hf = p->Hf; a.n0 = p->n0; a.M1 = p->M1; a.M2 = p->M2;
-        a.sinphi = (float)sin(p->tilt);
-        a.c1 = (float)(-1.0 / (4.0 * p->t1));
-        a.c2 = (float)(-1.0 / (4.0 * p->t2));
-        a.f1 = p->fM1;
-        a.ld = p->M1 + 1;
-        if (p->nproj > 4 * 512 || p->Wf > 8192)
-            return fail(p, LAMINO_EUNSUPPORTED, "Fourier projector supports up to 2048 angles");
-        int T2 = 8;
-        while (T2 > 1 && (size_t)(T2 + 2 * p->w - 1) * a.ld * sizeof(float2) > 150 * 1024) T2 /= 2;
-        while (p->M2 % T2) T2 /= 2;
-        a.T2 = T2;
-        size_t smem = (size_t)(T2 + 2 * p->w - 1) * a.ld * sizeof(float2) + sizeof(int) * (9 * (size_t)p->nproj + 1);
-        if (smem > 220 * 1024)
-            return fail(p, LAMINO_EUNSUPPORTED, "gridding transpose tile of %zu bytes exceeds shared memory", smem);
-        dim3 grid(p->M2 / T2, p->L);
-        ProfScope prof(p, "grid_t", s);
-        auto go = [&](auto kern) {
-            set_smem(kern, smem);
-            kern<<<grid, 512, smem, s>>>(a, Vt, Gt);
-        };
-        const bool e8 = p->fM1.e == 8;
-        switch (p->w) {
-            case 2: e8 ? go(k_grid_t<8, 2>) : go(k_grid_t<12, 2>); break;
-            case 3: e8 ? go(k_grid_t<8, 3>) : go(k_grid_t<12, 3>); break;
-            case 4: e8 ? go(k_grid_t<8, 4>) : go(k_grid_t<12, 4>); break;
-            case 5: e8 ? go(k_grid_t<8, 5>) : go(k_grid_t<12, 5>); break;
-            case 6: e8 ? go(k_grid_t<8, 6>) : go(k_grid_t<12, 6>); break;
-            case 7: e8 ? go(k_grid_t<8, 7>) : go(k_grid_t<12, 7>); break;
-            default: e8 ? go(k_grid_t<8, 8>) : go(k_grid_t<12, 8>); break;
+        {   // gridding transpose of planes [l0, l1): Vt -> Gt (absolute planes)
+            a.l0 = l0;
+            dim3 grid(p->M2 / T2, l1 - l0);
+            ProfScope prof(p, "grid_t", s);
+            auto go = [&](auto kern) {
+                set_smem(kern, gsmem);
+                kern<<<grid, 512, gsmem, s>>>(a, Vt, Gt);
+            };
+            const bool e8 = p->fM1.e == 8;
+            switch (p->w) {
+                case 2: e8 ? go(k_grid_t<8, 2>) : go(k_grid_t<12, 2>); break;
+                case 3: e8 ? go(k_grid_t<8, 3>) : go(k_grid_t<12, 3>); break;
+                case 4: e8 ? go(k_grid_t<8, 4>) : go(k_grid_t<12, 4>); break;
+                case 5: e8 ? go(k_grid_t<8, 5>) : go(k_grid_t<12, 5>); break;
+                case 6: e8 ? go(k_grid_t<8, 6>) : go(k_grid_t<12, 6>); break;
+                case 7: e8 ? go(k_grid_t<8, 7>) : go(k_grid_t<12, 7>); break;
+                default: e8 ? go(k_grid_t<8, 8>) : go(k_grid_t<12, 8>); break;
+            }
+            LAM_LAUNCH_CHECK(p, "gridding transpose kernel");
         }
-        LAM_LAUNCH_CHECK(p, "gridding transpose kernel");
     }
     {   // column pass transpose
         const FftDesc& f = p->fHf;

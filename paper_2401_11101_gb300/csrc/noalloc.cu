@@ -66,19 +66,14 @@ extern "C" int lamino_backproject_fourier_noalloc(lamino_plan_t p, const void* q
     void* base = nullptr;
     if ((rc = scratch_address(p, &base))) return rc;
 
-    // Run the Fourier kernels with the plan's workspaces pointed at the static
-    // array for the duration of this call (no buffer of the plan is touched or
-    // allocated), and without the tracing events (creating them would allocate).
-    void* keep_a = p->ws_a;
-    void* keep_b = p->ws_b;
+    // Run the Fourier kernels on views of the static array (no buffer of the
+    // plan is touched or allocated), without the tracing events (creating
+    // them would allocate).
+    const lam::FourierBufs fb = lam::fourier_bufs(p, base, static_cast<unsigned char*>(base) + a_al);
     const bool keep_prof = p->profiling;
-    p->ws_a = base;
-    p->ws_b = static_cast<unsigned char*>(base) + a_al;
     p->profiling = false;
-    rc = lam::launch_rowfft(p, q, dtype, static_cast<float2*>(p->ws_a), -1, stream);
-    if (!rc) rc = lam::run_fourier_after_rows(p, vol, stream);
-    p->ws_a = keep_a;
-    p->ws_b = keep_b;
+    rc = lam::launch_rowfft(p, q, dtype, fb.R, -1, stream);
+    if (!rc) rc = lam::run_fourier_after_rows(p, fb, vol, stream);
     p->profiling = keep_prof;
     return rc;
 }

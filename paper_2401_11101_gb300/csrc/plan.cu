@@ -151,6 +151,56 @@ FftDesc make_desc(int n) {
 // Greengard & Lee, SIAM Rev. 46 (2004)), written in cells: t = w R /(4 pi (R - 1/2)).
 double gauss_t(int w, double R) { return w * R / (4.0 * kPi * (R - 0.5)); }
 
+// Error model of the Gaussian USFFT along one axis of n voxels on an M-cell
+// grid with half-width w, as a mean square over the voxels. After the
+// deconvolution by psi(x), voxel x carries two relative errors: the kernel's
+// truncation at w cells, exp(-w^2/(4t)) amplified by 1/psi(x) ~ exp(4 pi^2 t
+// (x/M)^2), and the aliasing of the first image of the grid, psi(M - |x|) /
+// psi(x) = exp(-4 pi^2 t (1 - 2|x|/M)). With t from gauss_t both equal
+// exp(-pi w (R - 1)/(R - 1/2)) at the edge |x| = n/2 (2.3e-4 for w = 4, R = 2)
+// and fall off inside, so small axes (a larger share of voxels near the
+// edge) and R = 2 exactly (no spare oversampling) fare worst.
+double usfft_axis_err2(int n, int M, int w) {
+    const double t = gauss_t(w, (double)M / n), c = 4.0 * kPi * kPi * t;
+    double s = 0.0;
+    for (int i = 0; i < n; ++i) {
+        const double u = fabs((double)(i - n / 2)) / M;
+        const double e = exp(-w * (double)w / (4.0 * t) + c * u * u) + exp(-c * (1.0 - 2.0 * u));
+        s += e * e;
+    }
+    return s / n;
+}
+
+// Predicted relative L2 error of the Fourier form against the exact type-1
+// sum for a volume whose energy is spread evenly over the voxels (random
+// projections: the worst of the parity workloads). The root of the summed
+// axis models overestimates the measured FP32 error; measured / model was
+// 0.35-0.36 on random projections (8x8x8: 7.3e-5, 8x8x256: 1.02e-4,
+// 16x16x256: 8.8e-5 at w = 4), and that calibration is folded in here.
+constexpr double kErrCalib = 0.36;
+double usfft_err_est(int n0, int n1, int n2, int M1, int M2, int M3, int w, int wz) {
+    return kErrCalib * sqrt(usfft_axis_err2(n0, M1, w) + usfft_axis_err2(n1, M2, w) +
+                            usfft_axis_err2(n2, M3, wz));
+}
+
+// Half-widths the plan uses unless the caller sets them: the smallest
+// w in [4, 8] whose predicted error stays below kErrTarget (w = 4 for axes of
+// 24 voxels or more at R = 2, w = 5 for the smallest grids), and along x3 the
+// smallest wz whose axis term alone stays below 5 % of that (wz = 6; the x3
+// pass is cheap: 2 wz taps per plane and cell).
+constexpr double kErrTarget = 0.9e-4;
+void choose_widths(lamino_plan_t p, bool fix_w, bool fix_wz) {
+    if (!fix_wz) {
+        p->wz = 4;
+        while (p->wz < 8 && kErrCalib * sqrt(usfft_axis_err2(p->n2, p->M3, p->wz)) > 0.05 * kErrTarget) ++p->wz;
+    }
+    if (!fix_w) {
+        p->w = 4;
+        while (p->w < 8 && usfft_err_est(p->n0, p->n1, p->n2, p->M1, p->M2, p->M3, p->w, p->wz) > kErrTarget)
+            ++p->w;
+    }
+}
+
 // Deconvolution factor of one axis: the spread kernel exp(-d^2/(4t)) (d in
 // cells) has the continuous Fourier transform psi(x) = sqrt(4 pi t)/M *
 // exp(-4 pi^2 t (x/M)^2) at integer x; dividing the inverse DFT of the grid by
@@ -181,6 +231,7 @@ int upload(lamino_plan_t p, T** dst, const std::vector<T>& v, const char* what) 
     size_t bytes = sizeof(T) * std::max<size_t>(v.size(), 1);
     cudaError_t e = cudaMalloc((void**)dst, bytes);
     if (e != cudaSuccess) return cuda_fail(p, e, what);
+    p->table_bytes += bytes;
     if (!v.empty()) {
         e = cudaMemcpy(*dst, v.data(), sizeof(T) * v.size(), cudaMemcpyHostToDevice);
         if (e != cudaSuccess) return cuda_fail(p, e, what);
@@ -360,14 +411,15 @@ int validate_dtype_kind(lamino_plan_t p, int dtype, int kind) {
     return LAMINO_OK;
 }
 
-int fourier_workspace(lamino_plan_t p, size_t* a_bytes, size_t* b_bytes) {
-    size_t R = (size_t)p->nproj * p->H * p->Wf;    // row spectra
-    size_t V = (size_t)p->L * p->n0 * p->M2;       // planes after the x1 pass
-    size_t G = (size_t)p->L * p->nproj * p->Wf;    // half spectra, plane-major
-    G += G / colfft_chunk(p);                      // + chunk statistics (sum, max)
-    size_t P = (size_t)p->L * p->n1 * p->n0;       // deconvolved planes
-    *a_bytes = sizeof(float2) * std::max(R, V);
-    *b_bytes = sizeof(float2) * std::max(G, P);
+// Allocates (or keeps) the plan's two Fourier workspaces for its current
+// z chunking and returns their views.
+int fourier_buffers(lamino_plan_t p, FourierBufs* fb) {
+    size_t a, b;
+    fourier_workspace(p, &a, &b);
+    int rc = ensure_buffer(p, &p->ws_a, &p->ws_a_bytes, a, "Fourier workspace A");
+    if (rc) return rc;
+    if ((rc = ensure_buffer(p, &p->ws_b, &p->ws_b_bytes, b, "Fourier workspace B"))) return rc;
+    *fb = fourier_bufs(p, p->ws_a, p->ws_b);
     return LAMINO_OK;
 }
 
@@ -418,6 +470,11 @@ int lamino_plan(lamino_plan_t* out, int n0, int n1, int n2, int nproj, int det_w
     p->w = (opts && opts->usfft_w) ? opts->usfft_w : 4;
     p->wz = (opts && opts->usfft_wz) ? opts->usfft_wz : 6;
     p->grid_rows = (opts && opts->grid_rows > 0) ? opts->grid_rows : 0;
+    p->z_chunk = (opts && opts->z_chunk > 0) ? opts->z_chunk : 0;
+    if (opts && opts->z_chunk < 0) {
+        free_plan(p);
+        return fail(nullptr, LAMINO_EINVAL, "z_chunk must be >= 0");
+    }
     if (p->grid_rows & (p->grid_rows - 1)) {
         free_plan(p);
         return fail(nullptr, LAMINO_EINVAL, "grid_rows must be a power of two");
@@ -437,6 +494,8 @@ int lamino_plan(lamino_plan_t* out, int n0, int n1, int n2, int nproj, int det_w
     p->M1 = std::max(16, fft_size_at_least(2.0 * n0));
     p->M2 = std::max(16, fft_size_at_least(2.0 * n1));
     p->M3 = std::max(16, fft_size_at_least(2.0 * n2));
+    choose_widths(p, opts && opts->usfft_w, opts && opts->usfft_wz);
+    p->err_est = usfft_err_est(n0, n1, n2, p->M1, p->M2, p->M3, p->w, p->wz);
     p->t1 = gauss_t(p->w, (double)p->M1 / n0);
     p->t2 = gauss_t(p->w, (double)p->M2 / n1);
     p->t3 = gauss_t(p->wz, (double)p->M3 / n2);
@@ -480,6 +539,9 @@ int lamino_get_info(lamino_plan_t p, lamino_plan_info* info) {
     info->wp = p->Wp; info->wf = p->Wf; info->hf = p->Hf;
     info->m1 = p->M1; info->m2 = p->M2; info->m3 = p->M3;
     info->usfft_w = p->w; info->usfft_wz = p->wz; info->planes = p->L;
+    info->usfft_err_est = (float)p->err_est;
+    info->z_chunk = p->z_chunk;
+    info->plane_chunk = plane_chunk(p);
     return LAMINO_OK;
 }
 
@@ -507,13 +569,11 @@ static int fourier_common(lamino_plan_t p, const void* d, int dtype, float* vol,
     if (!p->fourier_ok) return fail(p, LAMINO_EUNSUPPORTED, "%s", p->fourier_why.c_str());
     if (kind >= 0 && !p->filter_ok)
         return fail(p, LAMINO_EUNSUPPORTED, "filter length %d is not a supported FFT length", p->Wp);
-    size_t a, b;
-    fourier_workspace(p, &a, &b);
-    int rc = ensure_buffer(p, &p->ws_a, &p->ws_a_bytes, a, "Fourier workspace A");
+    FourierBufs fb;
+    int rc = fourier_buffers(p, &fb);
     if (rc) return rc;
-    if ((rc = ensure_buffer(p, &p->ws_b, &p->ws_b_bytes, b, "Fourier workspace B"))) return rc;
-    if ((rc = launch_rowfft(p, d, dtype, (float2*)p->ws_a, kind, stream))) return rc;
-    return run_fourier_after_rows(p, vol, stream);
+    if ((rc = launch_rowfft(p, d, dtype, fb.R, kind, stream))) return rc;
+    return run_fourier_after_rows(p, fb, vol, stream);
 }
 
 int lamino_backproject_fourier(lamino_plan_t p, const void* q, int dtype, float* vol,
@@ -577,11 +637,9 @@ int lamino_fbp_host(lamino_plan_t p, int form, const void* d_host, int dtype, fl
     const size_t dvol = sizeof(float) * (size_t)p->n0 * p->n1 * p->n2;
     if ((rc = ensure_buffer(p, &p->h_in, &p->h_in_bytes, din, "device copy of projections"))) return rc;
     if ((rc = ensure_buffer(p, (void**)&p->h_vol, &p->h_vol_bytes, dvol, "device volume"))) return rc;
+    FourierBufs fb;
     if (form == LAMINO_FOURIER) {
-        size_t a, b;
-        fourier_workspace(p, &a, &b);
-        if ((rc = ensure_buffer(p, &p->ws_a, &p->ws_a_bytes, a, "Fourier workspace A"))) return rc;
-        if ((rc = ensure_buffer(p, &p->ws_b, &p->ws_b_bytes, b, "Fourier workspace B"))) return rc;
+        if ((rc = fourier_buffers(p, &fb))) return rc;
     } else {
         size_t need = sizeof(float) * (size_t)p->nproj * p->H * p->W;
         if ((rc = ensure_buffer(p, (void**)&p->q_buf, &p->q_buf_bytes, need, "filtered rows"))) return rc;
@@ -605,9 +663,9 @@ int lamino_fbp_host(lamino_plan_t p, int form, const void* d_host, int dtype, fl
         const long k0 = (long)p->nproj * c / nin, k1 = (long)p->nproj * (c + 1) / nin;
         LAM_CUDA(p, cudaStreamWaitEvent(stream, ev[1 + c], 0));
         if (form == LAMINO_FOURIER) {
-            if ((rc = launch_rowfft(p, p->h_in, dtype, (float2*)p->ws_a, kind, stream, k0 * p->H, k1 * p->H)))
+            if ((rc = launch_rowfft(p, p->h_in, dtype, fb.R, kind, stream, k0 * p->H, k1 * p->H)))
                 return rc;
-            if ((rc = launch_colfft(p, (int)k0, (int)k1, stream))) return rc;
+            if ((rc = launch_colfft(p, fb, (int)k0, (int)k1, stream))) return rc;
         } else {
             if ((rc = launch_filter(p, p->h_in, dtype, p->q_buf, kind, stream, k0 * p->H, k1 * p->H)))
                 return rc;
@@ -615,12 +673,11 @@ int lamino_fbp_host(lamino_plan_t p, int form, const void* d_host, int dtype, fl
     }
     cudaEvent_t* evo = ev + 1 + nin;
     if (form == LAMINO_FOURIER) {
-        if ((rc = launch_grid(p, stream))) return rc;
-        if ((rc = launch_colifft(p, stream))) return rc;
+        if ((rc = run_planes(p, fb, stream))) return rc;
         const size_t row = sizeof(float) * (size_t)p->n0, slice = row * p->n1;
         for (int v = 0; v < nout; ++v) {
             const int i10 = (int)((long)p->n1 * v / nout), i11 = (int)((long)p->n1 * (v + 1) / nout);
-            if ((rc = launch_zusfft(p, p->h_vol, i10, i11, stream))) return rc;
+            if ((rc = launch_zusfft(p, fb, p->h_vol, i10, i11, stream))) return rc;
             LAM_CUDA(p, cudaEventRecord(evo[v], stream));
             LAM_CUDA(p, cudaStreamWaitEvent(cs, evo[v], 0));
             // slab [x3][x2 in i10..i11)[x1]: n2 pieces of (i11 - i10) rows
@@ -647,13 +704,34 @@ int lamino_project(lamino_plan_t p, int form, const float* vol, float* d, cudaSt
     if (form == LAMINO_DIRECT) return launch_project_direct(p, vol, d, stream);
     if (form == LAMINO_FOURIER) {
         if (!p->fourier_ok) return fail(p, LAMINO_EUNSUPPORTED, "%s", p->fourier_why.c_str());
-        size_t a, b;
-        fourier_workspace(p, &a, &b);
-        if ((rc = ensure_buffer(p, &p->ws_a, &p->ws_a_bytes, a, "Fourier workspace A"))) return rc;
-        if ((rc = ensure_buffer(p, &p->ws_b, &p->ws_b_bytes, b, "Fourier workspace B"))) return rc;
-        return launch_project_fourier(p, vol, d, stream);
+        FourierBufs fb;
+        if ((rc = fourier_buffers(p, &fb))) return rc;
+        return launch_project_fourier(p, fb, vol, d, stream);
     }
     return fail(p, LAMINO_EINVAL, "unknown form %d", form);
+}
+
+int lamino_device_bytes(lamino_plan_t p, size_t* bytes) {
+    if (!p || !bytes) return fail(p, LAMINO_EINVAL, "lamino_device_bytes: NULL argument");
+    *bytes = p->table_bytes + sizeof(int) + p->ws_a_bytes + p->ws_b_bytes + p->q_buf_bytes +
+             p->q_pad_bytes + p->h_in_bytes + p->h_vol_bytes;
+    return LAMINO_OK;
+}
+
+int lamino_set_z_chunk(lamino_plan_t p, int z_chunk) {
+    if (!p) return fail(nullptr, LAMINO_EINVAL, "NULL plan");
+    if (z_chunk < 0) return fail(p, LAMINO_EINVAL, "z_chunk must be >= 0, not %d", z_chunk);
+    int rc = set_device(p);
+    if (rc) return rc;
+    if (z_chunk == p->z_chunk) return LAMINO_OK;
+    // the workspaces follow the new layout at the next call; cudaFree waits
+    // for the device, so nothing in flight still uses them
+    if (p->ws_a) LAM_CUDA(p, cudaFree(p->ws_a));
+    if (p->ws_b) LAM_CUDA(p, cudaFree(p->ws_b));
+    p->ws_a = p->ws_b = nullptr;
+    p->ws_a_bytes = p->ws_b_bytes = 0;
+    p->z_chunk = z_chunk;
+    return LAMINO_OK;
 }
 
 int lamino_workspace_bytes(lamino_plan_t p, int form, size_t* bytes) {

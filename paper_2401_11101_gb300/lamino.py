@@ -31,6 +31,7 @@ FORMS = {"direct": DIRECT, "fourier": FOURIER}
 EXPORTS = ("lamino_plan", "lamino_get_info", "lamino_filter", "lamino_backproject_direct",
            "lamino_backproject_fourier", "lamino_backproject_fourier_noalloc", "lamino_fbp", "lamino_fbp_host", "lamino_project",
            "lamino_status", "lamino_selftest_wait", "lamino_profile", "lamino_profile_read", "lamino_workspace_bytes",
+           "lamino_set_z_chunk", "lamino_device_bytes",
            "lamino_last_error", "lamino_destroy")
 
 
@@ -42,7 +43,8 @@ class LaminoError(RuntimeError):
 
 class _Opts(ctypes.Structure):
     _fields_ = [("usfft_w", ctypes.c_int), ("usfft_wz", ctypes.c_int),
-                ("wf", ctypes.c_int), ("hf", ctypes.c_int), ("grid_rows", ctypes.c_int)]
+                ("wf", ctypes.c_int), ("hf", ctypes.c_int), ("grid_rows", ctypes.c_int),
+                ("z_chunk", ctypes.c_int)]
 
 
 class _KTime(ctypes.Structure):
@@ -52,7 +54,9 @@ class _KTime(ctypes.Structure):
 class _Info(ctypes.Structure):
     _fields_ = [(n, ctypes.c_int) for n in
                 ("n0", "n1", "n2", "nproj", "det_w", "det_h", "wp", "wf", "hf", "m1", "m2", "m3",
-                 "usfft_w", "usfft_wz", "planes")]
+                 "usfft_w", "usfft_wz", "planes")] + [("usfft_err_est", ctypes.c_float),
+                                                       ("z_chunk", ctypes.c_int),
+                                                       ("plane_chunk", ctypes.c_int)]
 
 
 _lib = None
@@ -81,6 +85,8 @@ def load_library(path: str = LIB_PATH):
     lib.lamino_status.argtypes = [vp, vp]
     lib.lamino_selftest_wait.argtypes = [vp, ctypes.c_uint, vp]
     lib.lamino_workspace_bytes.argtypes = [vp, ci, ctypes.POINTER(sz)]
+    lib.lamino_set_z_chunk.argtypes = [vp, ci]
+    lib.lamino_device_bytes.argtypes = [vp, ctypes.POINTER(sz)]
     lib.lamino_profile.argtypes = [vp, ci]
     lib.lamino_profile_read.argtypes = [vp, ctypes.POINTER(_KTime), ci, ctypes.POINTER(ci)]
     lib.lamino_last_error.argtypes = [vp]
@@ -113,7 +119,7 @@ class Plan:
     """A reconstruction plan for one geometry (owns device tables/workspaces)."""
 
     def __init__(self, n0, n1, n2, nproj, det_w, det_h, tilt, angles=None, usfft_w=0,
-                 usfft_wz=0, wf=0, hf=0, grid_rows=0, device=None):
+                 usfft_wz=0, wf=0, hf=0, grid_rows=0, z_chunk=0, device=None):
         self._h = ctypes.c_void_p()
         ang_list = None
         if angles is not None:
@@ -124,7 +130,7 @@ class Plan:
         self._lib = load_library()
         idx = None if device is None else torch.device(device).index
         self.device = torch.device("cuda", torch.cuda.current_device() if idx is None else idx)
-        opts = _Opts(usfft_w, usfft_wz, wf, hf, grid_rows)
+        opts = _Opts(usfft_w, usfft_wz, wf, hf, grid_rows, z_chunk)
         ang = None
         if ang_list is not None:
             arr = (ctypes.c_double * nproj)(*ang_list)
@@ -137,6 +143,9 @@ class Plan:
         self.shape_vol = (n2, n1, n0)
         self.shape_proj = (nproj, det_h, det_w)
         self.nproj = nproj
+        self._read_info()
+
+    def _read_info(self):
         info = _Info()
         self._check(self._lib.lamino_get_info(self._h, ctypes.byref(info)))
         self.info = {f: getattr(info, f) for f, _ in _Info._fields_}
@@ -189,7 +198,9 @@ class Plan:
     def backproject_fourier_noalloc(self, q, out):
         """Fourier-form backprojection that allocates no device memory (its
         workspace is the library's fixed 64 MiB static array). `out` must be
-        given, since creating it would allocate."""
+        given, since creating it would allocate; q and out are used as they
+        are (a tensor of the wrong dtype, device or layout raises ValueError
+        rather than being copied), and the volume is written into `out`."""
         q = self._tensor(q, self.shape_proj, tuple(DTYPES), "q")
         v = self._tensor(out, self.shape_vol, (torch.float32,), "out")
         self._check(self._lib.lamino_backproject_fourier_noalloc(
@@ -228,9 +239,21 @@ class Plan:
                                              _stream(self.device)))
         return d
 
+    def set_z_chunk(self, z_chunk: int):
+        """k_v planes per Fourier chunk / slices per direct launch (0: none);
+        frees the Fourier workspaces, which the next call re-allocates."""
+        self._check(self._lib.lamino_set_z_chunk(self._h, int(z_chunk)))
+        self._read_info()
+
     def workspace_bytes(self, form="fourier") -> int:
         b = ctypes.c_size_t()
         self._check(self._lib.lamino_workspace_bytes(self._h, _form(form), ctypes.byref(b)))
+        return int(b.value)
+
+    def device_bytes(self) -> int:
+        """Device memory this plan holds now (tables + allocated workspaces)."""
+        b = ctypes.c_size_t()
+        self._check(self._lib.lamino_device_bytes(self._h, ctypes.byref(b)))
         return int(b.value)
 
     def profile(self, enable: bool = True):

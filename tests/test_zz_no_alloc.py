@@ -36,6 +36,40 @@ def _rel(a, b):
     return float((a - b).norm() / b.norm())
 
 
+def test_noalloc_first_on_fresh_plan_allocates_nothing(L):
+    # a fresh plan whose Fourier workspaces were never allocated: the entry
+    # point runs before any allocating call, and device memory does not move
+    # across a call once the first one (which also loads the kernels and looks
+    # up the static array) is done
+    g = I.Geometry(48, 48, 24, 30, 28, 72, math.radians(25.0))
+    q = torch.as_tensor(I.random_projections(g, 6), dtype=torch.float32).cuda()
+    with L.Plan(g.n0, g.n1, g.n2, g.nproj, g.det_w, g.det_h, g.tilt) as p:
+        out = torch.empty(p.shape_vol, dtype=torch.float32, device="cuda")
+        p.backproject_fourier_noalloc(q, out)
+        torch.cuda.synchronize()
+        first = out.clone()
+        free0 = torch.cuda.mem_get_info()[0]
+        out.fill_(float("nan"))
+        p.backproject_fourier_noalloc(q, out)
+        torch.cuda.synchronize()
+        free1 = torch.cuda.mem_get_info()[0]
+        assert free1 == free0, f"device free memory moved by {free0 - free1} bytes"
+        assert torch.equal(out, first)
+        ref = p.backproject_fourier(q)          # allocates the plan's own workspaces
+        assert _rel(out, ref) <= 1e-6
+
+
+def test_noalloc_rejects_tensors_it_would_have_to_convert(L):
+    g = I.Geometry(16, 16, 8, 6, 10, 24, math.radians(20.0))
+    with L.Plan(g.n0, g.n1, g.n2, g.nproj, g.det_w, g.det_h, g.tilt) as p:
+        q = torch.zeros(p.shape_proj, dtype=torch.float32, device="cuda")
+        out = torch.empty(p.shape_vol, dtype=torch.float32, device="cuda")
+        for bad_q, bad_out in ((q.double(), out), (q, out.double()), (q.cpu(), out),
+                               (q, torch.empty(p.shape_vol[::-1], device="cuda").transpose(0, 2))):
+            with pytest.raises(ValueError):
+                p.backproject_fourier_noalloc(bad_q, bad_out)
+
+
 def test_noalloc_matches_fourier_twice(L):
     g, _, d = I.make_projections("c1")
     with L.Plan(g.n0, g.n1, g.n2, g.nproj, g.det_w, g.det_h, g.tilt) as p:
