@@ -11,7 +11,10 @@ One step = one pass of the whole hot path over the HBM-resident projections:
                Gaussian gridding + x1 inverse FFT, x2 inverse FFT, x3 USFFT;
   direct FBP:  row filter, TMA-staged bilinear backprojection.
 `value` is the Fourier-form FBP throughput in GVox/s (the volume size over the
-Fourier part of the step); the direct form's figure is reported beside it.
+Fourier part of the step); the direct form's figure is reported beside it,
+with the two forms' relative L2 gap. The metric's qualifier (the forms agree
+to relL2 <= 1e-3) is shown on a band-limited input of the same geometry
+(`qualifier`: c2b, whose own discretisation gap is below 1e-3).
 
 Usage: python bench.py [--gpus N --steps K --warmup W] [--impl reference]
 Multi-GPU (torchrun): every rank reconstructs its own slab (independent
@@ -47,7 +50,13 @@ WORKLOADS = {
           "blobs, 0.5% noise, Shepp-Logan",
     "c3": "2048x2048x512 slab, 1800 projections over 360 deg, detector 512x2048 stored FP16, "
           "tilt 18 deg, 5000 ellipsoids + 2% dense spheres, Poisson 1e4 photons, Shepp-Logan",
+    "c2b": "512x512x256 slab, 720 projections over 360 deg, detector 256x768, tilt 20 deg, "
+           "40 Gaussian blobs sigma~U[12,20] inside the detector's field of view, noise-free, "
+           "Shepp-Logan (band-limited: the forms' own gap is below 1e-3)",
 }
+# shared-memory reduction pipe: 32 banks, one 32-bit reduction per bank and
+# clock; a complex tap of the gridding is two of them (real, imaginary)
+SMEM_RED_LANES_PER_CLK = 32
 FP32_LANES_PER_SM = 128
 N_SMS = 152
 
@@ -61,9 +70,11 @@ def parse():
     ap.add_argument("--workload", default="c2", choices=sorted(WORKLOADS))
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
-    ap.add_argument("--cpu-columns", type=int, default=32)
+    ap.add_argument("--cpu-columns", type=int, default=16)
+    ap.add_argument("--z-chunk", type=int, default=0)
+    ap.add_argument("--no-qualifier", action="store_true")
     ap.add_argument("--no-serve", action="store_true")
-    ap.add_argument("--serve-requests", type=int, default=32)
+    ap.add_argument("--serve-requests", type=int, default=200)
     ap.add_argument("--serve-rate", type=float, default=20.0)
     ap.add_argument("--no-cg", action="store_true")
     ap.add_argument("--cg-iters", type=int, default=50)
@@ -152,6 +163,14 @@ class ClockSampler:
                 "reasons": reasons, "samples": len(rows)}
 
 
+def grid_taps(p_info, g, planes=None) -> int:
+    """Complex taps the gridding spreads per launch: every point (angle k,
+    column frequency m, the Nyquist column dropped) of every plane it grids
+    reaches (2w)^2 cells of the oversampled plane."""
+    L = p_info["planes"] if planes is None else planes
+    return L * g.nproj * (p_info["wf"] - 1) * (2 * p_info["usfft_w"]) ** 2
+
+
 def kernel_algorithmic(p_info, g, esz_in=4):
     """Algorithmic bytes (one read of each input, one write of each output) or
     FP32 flops per launch of every kernel of the hot path."""
@@ -201,42 +220,95 @@ def ncu_traffic(workload: str):
 
 # --------------------------------------------------------------------- CPU oracle
 
-def oracle_fourier_sample(d_cpu: np.ndarray, g, ncols: int, seed: int = 7):
-    """The FP64 oracle's Fourier-form FBP on a bounded sample: the filter of
-    every row, the 2D DFT of every projection, the exact type-1 sum on ncols
-    whole columns. Returns (seconds, voxels, threads)."""
-    from oracle import lamino_oracle as O
+def sample_columns(g, n, seed):
     rng = np.random.default_rng(seed)
-    cols = np.stack([rng.integers(0, g.n0, ncols), rng.integers(0, g.n1, ncols)], 1).astype(np.int32)
+    return np.stack([rng.integers(0, g.n0, n), rng.integers(0, g.n1, n)], 1).astype(np.int32)
+
+
+def oracle_sample(d_cpu: np.ndarray, g, ncols: int, seed: int = 7, threads: int | None = None):
+    """The FP64 oracle's FBP of both forms on a bounded sample: the row filter
+    of every projection (a fixed cost), then the Fourier form (the exact sum,
+    evaluated in detector space) and the direct form on ncols whole columns.
+    Returns the times, the columns and both forms' values."""
+    from oracle import lamino_oracle as O
+    O.set_num_threads(threads or os.cpu_count() or 1)
+    cols = sample_columns(g, ncols, seed)
     t0 = time.perf_counter()
     q = O.filter_rows(d_cpu, g, "shepp")
-    O.backproject_fourier_columns(q, g, cols)
-    dt = time.perf_counter() - t0
-    return dt, ncols * g.n2, O.num_threads()
+    t1 = time.perf_counter()
+    of = O.backproject_trig_columns(q, g, cols)
+    t2 = time.perf_counter()
+    od = O.backproject_direct_columns(q, g, cols)
+    t3 = time.perf_counter()
+    out = {"fixed_s": t1 - t0, "fourier_col_s": (t2 - t1) / ncols, "direct_col_s": (t3 - t2) / ncols,
+           "threads": O.num_threads(), "cols": cols, "fourier": of, "direct": od}
+    O.set_num_threads(os.cpu_count() or 1)
+    return out
+
+
+def oracle_baseline(d_cpu: np.ndarray, g, ncols: int) -> dict:
+    """cpu_baseline: the oracle's Fourier-form FBP throughput extrapolated to
+    the whole volume from its fixed cost and its cost per column (all host
+    threads), with the single-thread time and the direct form beside it."""
+    s = oracle_sample(d_cpu, g, ncols)
+    ncol_all = g.n0 * g.n1
+    full_f = s["fixed_s"] + s["fourier_col_s"] * ncol_all
+    full_d = s["fixed_s"] + s["direct_col_s"] * ncol_all
+    one = oracle_sample(d_cpu, g, 1, seed=8, threads=1)
+    full_f1 = one["fixed_s"] + one["fourier_col_s"] * ncol_all
+    return {"value": g.nvox / full_f / 1e9, "unit": "GVox/s", "cores": s["threads"], "kind": "oracle",
+            "sample": (f"FP64 oracle, Fourier form (exact type-1 sum, detector-space evaluation): filter "
+                       f"of all {g.nproj * g.det_h} rows ({s['fixed_s']:.2f} s) + {ncols} whole columns "
+                       f"x {g.n2} slices ({s['fourier_col_s']:.3f} s per column), extrapolated to all "
+                       f"{ncol_all} columns = {full_f:.0f} s"),
+            "fixed_s": s["fixed_s"], "per_column_s": s["fourier_col_s"], "full_volume_s": full_f,
+            "single_thread": {"fixed_s": one["fixed_s"], "per_column_s": one["fourier_col_s"],
+                              "full_volume_s": full_f1, "gvox_s": g.nvox / full_f1 / 1e9},
+            "direct_form": {"per_column_s": s["direct_col_s"], "full_volume_s": full_d,
+                            "gvox_s": g.nvox / full_d / 1e9},
+            "_sample": s}
 
 
 # --------------------------------------------------------------------- serving
 
 def run_serving(n: int, rate: float, device: int, seed: int = 5) -> dict:
-    """Mixed stream of FBP requests (Poisson arrivals): volumes from {128^3,
-    256^2x128, 512^2x256, 1024^2x256}, 180-1800 angles, tilt U[10,40] deg,
-    detector width 1.5 x volume width, FP16 ellipsoid-phantom projections
-    (40 ellipsoids per request). Returns the latency / throughput summary."""
+    """Mixed stream of FBP requests with Poisson arrivals, served live: a client
+    thread submits each request at its arrival time to a running server
+    (Server.start / submit / stop). Volumes from {128^3, 256^2x128, 512^2x256,
+    1024^2x256}, 180-1800 angles, tilt U[10,40] deg, detector width 1.5 x volume
+    width, FP16 projections on pinned host memory, Fourier form, volumes copied
+    back to pinned host buffers. Each request's input is the first nproj
+    projections of one pinned projection set per size class (1800 angles of 40
+    ellipsoids): the shapes, transfers and work of the mixed stream, without
+    pinning separate data for every request (about 70 GB for 200)."""
     from paper_2401_11101_gb300 import serve as S
     reqs = S.mixed_requests(n, rate, seed)
     t0 = time.perf_counter()
+    tmpl = {}
     for r in reqs:
-        g = I.Geometry(r.n0, r.n1, r.n2, r.nproj, r.det_h, r.det_w, r.tilt)
-        prm = I.ellipsoid_params(g, 40, seed=1000 + r.rid, max_axis=max(4.0, r.n2 / 8.0))
-        d = I.project_boxed(prm, g, device=f"cuda:{device}", dtype=torch.float32)
-        r.d = d.half().cpu().pin_memory()
+        cls = (r.n0, r.n1, r.n2)
+        if cls not in tmpl:
+            g = I.Geometry(r.n0, r.n1, r.n2, 1800, r.n2, r.det_w, math.radians(25.0))
+            prm = I.ellipsoid_params(g, 40, seed=1000 + len(tmpl), max_axis=max(4.0, r.n2 / 8.0))
+            d = I.project_boxed(prm, g, device=f"cuda:{device}", dtype=torch.float32)
+            tmpl[cls] = d.half().cpu().pin_memory()
+            del d
+        r.d = tmpl[cls][: r.nproj]
         r.form = "fourier"
     gen_s = time.perf_counter() - t0
-    backend = S.CudaBackend(device, slots=4, keep_volumes=True)
-    # plans and workspaces of every geometry class stay resident across requests
-    rep = S.Server(backend, slots=4).run(reqs)
+    backend = S.CudaBackend(device, slots=4, keep_volumes=False)
+    srv = S.Server(backend, slots=4)
+    srv.start()
+    start = time.perf_counter()
+    for r in reqs:
+        wait = r.arrival - (time.perf_counter() - start)
+        if wait > 0:
+            time.sleep(wait)
+        srv.submit(r)
+    rep = srv.stop()
     out = rep.summary(reqs)
     out.update({"rate_req_s": rate, "slots": 4, "form": "fourier", "input_generation_s": gen_s,
+                "mode": "live: a client thread submits at Poisson arrival times while the loop thread runs",
                 "workload": "mixed volumes {128^3, 256^2x128, 512^2x256, 1024^2x256}, "
                             "180-1800 angles, tilt U[10,40] deg, det 1.5 n0 x n2, FP16"})
     return out
@@ -274,19 +346,21 @@ def run_reference(args, geom, d):
     ws, rank, _ = dist_env()
     if rank != 0:
         return
-    from oracle import lamino_oracle as O
     d_cpu = d.cpu().numpy()
     ncols = 4
     for _ in range(args.warmup):
-        oracle_fourier_sample(d_cpu, geom, ncols)
-    times, vox = [], 0
+        oracle_sample(d_cpu, geom, ncols)
+    times, thr = [], 1
     for _ in range(args.steps):
-        dt, vox, thr = oracle_fourier_sample(d_cpu, geom, ncols)
-        times.append(dt)
+        t0 = time.perf_counter()
+        s = oracle_sample(d_cpu, geom, ncols)
+        times.append(time.perf_counter() - t0)
+        thr = s["threads"]
     t = sum(times) / len(times)
+    vox = ncols * geom.n2
     val = vox / t / 1e9
-    sample = (f"Fourier-form FBP by the FP64 oracle: filter of all {geom.nproj * geom.det_h} rows, "
-              f"2D DFT of all {geom.nproj} projections, exact type-1 sum on {ncols} columns x "
+    sample = (f"FBP of both forms by the FP64 oracle: filter of all {geom.nproj * geom.det_h} rows, "
+              f"then the Fourier form (exact type-1 sum) and the direct form on {ncols} whole columns x "
               f"{geom.n2} slices = {vox} voxels per step")
     line = {"impl": "reference", "metric": METRIC, "value": val, "unit": "GVox/s",
             "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
@@ -300,11 +374,37 @@ def run_reference(args, geom, d):
     print(json.dumps(line), flush=True)
 
 
+def gvox_gap(a: torch.Tensor, b: torch.Tensor) -> float:
+    return float((a - b).double().norm() / a.double().norm())
+
+
+def run_qualifier(plan_kw, dev) -> dict:
+    """The metric's qualifier on the band-limited c2b input: both forms on the
+    GPU (full volume) and the FP64 oracle's own gap on sampled columns."""
+    from paper_2401_11101_gb300 import lamino as L
+    g, _, d = I.make_projections("c2b", device=str(dev))
+    with L.Plan(g.n0, g.n1, g.n2, g.nproj, g.det_w, g.det_h, g.tilt, **plan_kw) as p:
+        vf = p.fbp(d, form="fourier", kind="shepp")
+        vd = p.fbp(d, form="direct", kind="shepp")
+        p.status()
+    out = {"workload": "c2b: " + WORKLOADS["c2b"], "gap_relL2_gpu": gvox_gap(vf, vd)}
+    s = oracle_sample(d.cpu().numpy(), g, 16, seed=43)
+    cols = s["cols"]
+    gf = np.stack([vf[:, i1, i0].cpu().numpy() for i0, i1 in cols])
+    gd = np.stack([vd[:, i1, i0].cpu().numpy() for i0, i1 in cols])
+    rel = lambda a, b: float(np.linalg.norm(a - b) / np.linalg.norm(a))
+    out.update({"gap_relL2_gpu_sampled": rel(gf, gd), "gap_relL2_oracle_sampled": rel(s["fourier"], s["direct"]),
+                "fourier_vs_oracle_sampled": rel(s["fourier"], gf), "direct_vs_oracle_sampled": rel(s["direct"], gd),
+                "sampled_columns": len(cols)})
+    return out
+
+
 def run_ours(args, geom, d):
     from paper_2401_11101_gb300 import lamino as L
     ws, rank, local = dist_env()
     dev = torch.device("cuda", local)
-    plan = L.Plan(geom.n0, geom.n1, geom.n2, geom.nproj, geom.det_w, geom.det_h, geom.tilt)
+    plan_kw = {"z_chunk": args.z_chunk} if args.z_chunk else {}
+    plan = L.Plan(geom.n0, geom.n1, geom.n2, geom.nproj, geom.det_w, geom.det_h, geom.tilt, **plan_kw)
     info = plan.info
     vol_f = torch.empty(plan.shape_vol, dtype=torch.float32, device=dev)
     vol_d = torch.empty(plan.shape_vol, dtype=torch.float32, device=dev)
@@ -353,6 +453,7 @@ def run_ours(args, geom, d):
     nvox = geom.nvox
     value = job_gvox_s(nvox, ws, t_f)
     value_d = job_gvox_s(nvox, ws, t_d)
+    gap_gpu = gvox_gap(vol_f, vol_d)
 
     # per-kernel live timing and roofline
     per = {}
@@ -368,17 +469,20 @@ def run_ours(args, geom, d):
     for name, v in per.items():
         avg = sum(v) / len(v)
         kind, amount = alg.get(name, ("hbm", 0))
+        # a z-chunked form launches a kernel once per chunk: the amounts are per step
+        steps_launches = len(v) / args.steps
+        amount_l = amount / steps_launches
         if kind == "hbm":
-            ach = amount / (avg * 1e-3) / 1e9
+            ach = amount_l / (avg * 1e-3) / 1e9
             peak = float(peaks.get("hbm_gbs", 6800.0))
             unit = "GB/s"
         else:
-            ach = amount / (avg * 1e-3) / 1e12
+            ach = amount_l / (avg * 1e-3) / 1e12
             peak = alu_peak
             unit = "TFLOP/s"
         kernels[name] = {"launches": len(v), "avg_ms": round(avg, 4), "share": round(sum(v) / total, 4),
                          "bound": kind, "achieved": round(ach, 2), "peak": round(peak, 1), "unit": unit,
-                         "frac": round(ach / peak, 4), "algorithmic": amount}
+                         "frac": round(ach / peak, 4), "algorithmic": amount_l}
 
     def roof(name):
         k = kernels[name]
@@ -387,9 +491,24 @@ def run_ours(args, geom, d):
                 "unit": k["unit"], "frac": k["frac"], "traffic": tr,
                 "peak_source": f"{peaks_src} ({'hbm_gbs' if k['bound'] == 'hbm' else 'SMs x 128 FP32 lanes x 2 x sm_max_mhz'})"}
 
-    dominant = max(kernels, key=lambda n: kernels[n]["share"])
+    # the headline path is the Fourier form: its dominant kernel is the gridding
     fourier_names = [n for n in kernels if n in ("filter_rowfft", "colfft", "grid", "colifft", "zusfft")]
     dom_f = max(fourier_names, key=lambda n: kernels[n]["share"])
+    roofline = roof(dom_f)
+    if "grid" in kernels:
+        g_ms = kernels["grid"]["avg_ms"]
+        taps = grid_taps(info, geom) / (len(per["grid"]) / args.steps)
+        red_peak = N_SMS * SMEM_RED_LANES_PER_CLK / 2 * sm_mhz_max * 1e6       # complex taps / s
+        ach_taps = taps / (g_ms * 1e-3)
+        roofline["bounds"] = {
+            "hbm": {"achieved": kernels["grid"]["achieved"], "peak": kernels["grid"]["peak"], "unit": "GB/s",
+                    "frac": kernels["grid"]["frac"], "per_launch_bytes": kernels["grid"]["algorithmic"]},
+            "smem_reduction": {"achieved": round(ach_taps / 1e9, 1), "peak": round(red_peak / 1e9, 1),
+                               "unit": "Gtap/s", "frac": round(ach_taps / red_peak, 4),
+                               "per_launch_taps": taps,
+                               "peak_source": "152 SMs x 32 shared-memory banks x sm_max_mhz / 2 "
+                                              "(one 32-bit reduction per bank and clock; two per complex tap)"}}
+    roofline_direct = roof("direct") if "direct" in kernels else None
 
     # end to end through the C ABI on host buffers (Fourier form)
     e2e = None
@@ -418,17 +537,31 @@ def run_ours(args, geom, d):
     cg = None
     if not args.no_cg:
         cg = run_cg(args.cg_iters, local)
+    qual = None
+    if not args.no_qualifier and args.workload in ("c2", "c2b"):
+        qual = run_qualifier(plan_kw, dev)
 
     cpu = None
+    gap_oracle = None
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:
-        dt, vox, thr = oracle_fourier_sample(d.cpu().numpy(), geom, args.cpu_columns)
-        cpu = {"value": vox / dt / 1e9, "unit": "GVox/s", "cores": thr, "kind": "oracle",
-               "sample": (f"Fourier-form FBP by the FP64 oracle: filter of all "
-                          f"{geom.nproj * geom.det_h} rows, 2D DFT of all {geom.nproj} projections, "
-                          f"exact type-1 sum on {args.cpu_columns} columns x {geom.n2} slices "
-                          f"= {vox} voxels, {dt:.1f} s")}
+        cpu = oracle_baseline(d.cpu().numpy(), geom, args.cpu_columns)
+        s = cpu.pop("_sample")
+        cols = s["cols"]
+        vf = np.stack([vol_f[:, i1, i0].cpu().numpy() for i0, i1 in cols])
+        vd = np.stack([vol_d[:, i1, i0].cpu().numpy() for i0, i1 in cols])
+        rel = lambda a, b: float(np.linalg.norm(a - b) / np.linalg.norm(a))
+        gap_oracle = {"gap_relL2_oracle_sampled": rel(s["fourier"], s["direct"]),
+                      "gap_relL2_gpu_sampled": rel(vf, vd),
+                      "fourier_vs_oracle_sampled": rel(s["fourier"], vf),
+                      "direct_vs_oracle_sampled": rel(s["direct"], vd), "sampled_columns": len(cols)}
 
     if rank == 0:
+        forms = {"fourier": {"gvox_s": value, "ms": t_f},
+                 "direct": {"gvox_s": value_d, "ms": t_d, "roofline": roofline_direct},
+                 "fourier_over_direct": t_d / t_f,
+                 "gap_relL2": gap_gpu}
+        if gap_oracle:
+            forms.update(gap_oracle)
         line = {"metric": METRIC, "value": value, "unit": "GVox/s", "n_gpus": ws, "steps": args.steps,
                 "warmup": args.warmup, "ms_per_step": t_f + t_d, "higher_is_better": True,
                 "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
@@ -436,11 +569,11 @@ def run_ours(args, geom, d):
                 "config": {"workload": f"{args.workload}: {WORKLOADS[args.workload]}",
                            "parallelism": f"replicas x{ws} (independent slabs)",
                            "l2": "inputs larger than L2 and a 256 MB L2 flush between steps",
-                           "usfft": {"R": 2, "w_xy": info["usfft_w"], "w_z": info["usfft_wz"]}},
-                "forms": {"fourier": {"gvox_s": value, "ms": t_f},
-                          "direct": {"gvox_s": value_d, "ms": t_d},
-                          "fourier_over_direct": t_d / t_f},
-                "roofline": roof(dominant), "roofline_fourier": roof(dom_f),
+                           "usfft": {"R": 2, "w_xy": info["usfft_w"], "w_z": info["usfft_wz"],
+                                     "err_est": info["usfft_err_est"]},
+                           "z_chunk": info["z_chunk"], "plane_chunk": info["plane_chunk"]},
+                "forms": forms, "qualifier": qual,
+                "roofline": roofline,
                 "kernels": kernels, "gpu_launches": len(recs),
                 "clocks": clk, "e2e": e2e, "cpu_baseline": cpu, "serve": serve, "cg": cg}
         print(json.dumps(line), flush=True)
