@@ -60,6 +60,7 @@ struct lamino_plan_s {
                                          // direct launch (0: no chunking)
     double t1 = 0, t2 = 0, t3 = 0;       // Gaussian widths (grid cells^2) per axis
     lam::FftDesc fWp, fWf, fHf, fM1, fM2, fM3;
+    lam::FftDesc fWp3, fWf3;             // Wp/3 and Wf/3 (decimated-by-3 row kernels; n = 0 if unused)
     int zmax = 0;                        // taps per cell of the x3 gridding table
 
     // device tables (owned)
@@ -86,6 +87,7 @@ struct lamino_plan_s {
     float* q_pad = nullptr; size_t q_pad_bytes = 0; // rows padded to a 16-byte pitch (TMA)
     void* h_in = nullptr; size_t h_in_bytes = 0;   // device copy of host input
     float* h_vol = nullptr; size_t h_vol_bytes = 0;
+    void* lent = nullptr; size_t lent_bytes = 0;   // caller-owned workspace (lamino_set_workspace)
     cudaStream_t copy_stream = nullptr;            // host pipeline: copies overlap kernels
     std::vector<cudaEvent_t> pipe_ev;              // host pipeline: chunk events
 
@@ -125,6 +127,12 @@ void set_global_error(const char* msg);
     } while (0)
 
 int ensure_buffer(lamino_plan_t p, void** buf, size_t* have, size_t need, const char* what);
+// Workspaces of the direct form: the filtered rows (lamino_fbp) and the copy of
+// the projections at a 16-byte row pitch (TMA), from the caller's lent buffer
+// (rows at 0, padded copy at lent_pad_offset) or plan-owned allocations.
+int rows_buffer(lamino_plan_t p, float** q);
+int pad_buffer(lamino_plan_t p, size_t need, float** q);
+inline size_t lent_align(size_t b) { return (b + 255) / 256 * 256; }
 int set_device(lamino_plan_t p);
 
 // tracing: bracket a launch with events when profiling is on
@@ -427,6 +435,71 @@ __device__ __forceinline__ void twiddle16(float2* v, const float2* __restrict__ 
         v[4 * q + 1] = cmul(v[4 * q + 1], cmul(wq, w1));
         v[4 * q + 2] = cmul(v[4 * q + 2], cmul(wq, w2));
         v[4 * q + 3] = cmul(v[4 * q + 3], cmul(wq, w3));
+    }
+}
+
+// v[c] *= w^(u c) for c = 1..7, w = exp(s 2 pi i / n), from the table
+// tw[j] = exp(-2 pi i j / n) (4 u < n): three table loads and four products.
+__device__ __forceinline__ void twiddle8(float2* v, const float2* __restrict__ tw, int u, float s) {
+    const float sg = (s > 0.f) ? -1.f : 1.f;
+    float2 w1 = __ldg(tw + u), w2 = __ldg(tw + 2 * u), w4 = __ldg(tw + 4 * u);
+    w1.y *= sg;
+    w2.y *= sg;
+    w4.y *= sg;
+    const float2 w3 = cmul(w2, w1);
+    v[1] = cmul(v[1], w1);
+    v[2] = cmul(v[2], w2);
+    v[3] = cmul(v[3], w3);
+    v[4] = cmul(v[4], w4);
+    v[5] = cmul(v[5], cmul(w4, w1));
+    v[6] = cmul(v[6], cmul(w4, w2));
+    v[7] = cmul(v[7], cmul(w4, w3));
+}
+
+// 256-point FFT of the sequence x (shared memory, natural order in and out,
+// unnormalised, exponent sign s) by the 32 lanes of one warp: 256 = 8 x 32.
+// With n = 32a + t and k = c + 8e,
+//   X[c + 8e] = sum_t w32^(te) [w256^(tc) sum_a x[32a + t] w8^(ac)].
+// Lane t takes the 8-point DFT over a and its twiddles; after a transpose
+// through x (row c rotated by 4c slots, so that the column reads below hit
+// 16 distinct 8-byte slots per half-warp), lane (c, r) = (lane / 4, lane % 4)
+// takes the 8-point DFT D_r over the samples t = 4m + r of row c and the
+// twiddles w32^(re); a radix-4 DFT over r between the lanes of a quad (two
+// shuffle butterflies, as in fft1024_pair) gives X[c + 8e + 64q], lane r
+// producing q = 2 (r % 2) + r / 2. tw: exp(-2 pi i u / 256), u in [0, 256).
+__device__ __forceinline__ void fft256_warp(float2* x, const float2* __restrict__ tw, float s, int lane) {
+    float2 v[8];
+#pragma unroll
+    for (int a = 0; a < 8; ++a) v[a] = x[32 * a + lane];
+    bfly<8>(v, s);
+    twiddle8(v, tw, lane, s);
+    __syncwarp();
+#pragma unroll
+    for (int c = 0; c < 8; ++c) x[32 * c + ((lane + 4 * c) & 31)] = v[c];
+    __syncwarp();
+    const int c = lane >> 2, r = lane & 3;
+#pragma unroll
+    for (int m = 0; m < 8; ++m) v[m] = x[32 * c + ((4 * m + r + 4 * c) & 31)];
+    bfly<8>(v, s);
+    twiddle8(v, tw, 8 * r, s);
+    const int b1 = r >> 1, b0 = r & 1;
+#pragma unroll
+    for (int e = 0; e < 8; ++e) {
+        float2 o;
+        o.x = __shfl_xor_sync(0xffffffffu, v[e].x, 2);
+        o.y = __shfl_xor_sync(0xffffffffu, v[e].y, 2);
+        float2 t = b1 ? csub(o, v[e]) : cadd(v[e], o);
+        if (b1 & b0) t = cmul_si(t, s);
+        v[e] = t;
+    }
+    __syncwarp();   // every read of x precedes the writes below
+    const int q = 2 * b0 + b1;
+#pragma unroll
+    for (int e = 0; e < 8; ++e) {
+        float2 o;
+        o.x = __shfl_xor_sync(0xffffffffu, v[e].x, 1);
+        o.y = __shfl_xor_sync(0xffffffffu, v[e].y, 1);
+        x[c + 8 * e + 64 * q] = b0 ? csub(o, v[e]) : cadd(v[e], o);
     }
 }
 

@@ -130,6 +130,168 @@ __global__ void __launch_bounds__(512, 1) k_rowfft(const Tin* __restrict__ d, fl
     }
 }
 
+// ---------------------------------------------------------------------------
+// Rows of length 3N (N = 256 or 512, one warp per N-point transform). A row
+// pair z = a + i b is kept 3-way decimated in shared memory, buffer b holding
+// z[3i + b] (b = 0, 1, 2; buffers LB slots apart). A length-3N DFT is then
+// three N-point DFTs of the buffers (one warp each, register-resident:
+// fft256_warp / fft512_warp) and a radix-3 step per frequency k < N:
+//   X[k + N j] = sum_b exp(-2 pi i b k / 3N) Y_b[k] exp(-2 pi i b j / 3)
+// (decimation in time), which reads and writes the three buffers at index k
+// only. The filter multiplies X by H and inverts the radix-3 step in the same
+// pass, so forward transform, multiplication and inverse transform meet in
+// registers; the 3N-point Stockham stages (six shared-memory round trips each
+// way) become two warp transposes each way.
+// ---------------------------------------------------------------------------
+template <int N>
+__device__ __forceinline__ void fft_warp(float2* x, const float2* __restrict__ tw, float s, int lane) {
+    static_assert(N == 256 || N == 512, "warp FFT length");
+    if constexpr (N == 256) fft256_warp(x, tw, s, lane);
+    else fft512_warp(x, tw, s, lane);
+}
+
+// barrier of the 96 threads (three warps) of sequence `seq` of a block
+__device__ __forceinline__ void seq_sync(int seq) {
+    asm volatile("bar.sync %0, 96;" ::"r"(seq + 1) : "memory");
+}
+
+// Rows rA and rA + 1 (if hasB) placed at offset `off` of a length-3NB row,
+// 3-way decimated into buf (buffers LB apart), zero elsewhere.
+template <typename Tin>
+__device__ __forceinline__ void load_rows3(const Tin* __restrict__ d, float2* buf, int LB, int NB,
+                                           long rA, bool hasB, int W, int off, int t96) {
+    const size_t ra = (size_t)rA * W, rb = ra + W;
+    for (int j = t96; j < 3 * NB; j += 96) {
+        const int src = j - off;
+        const bool in = src >= 0 && src < W;
+        const float a = in ? load_f(d, ra + src) : 0.f;
+        const float b = (in && hasB) ? load_f(d, rb + src) : 0.f;
+        buf[(j % 3) * LB + j / 3] = make_float2(a, b);
+    }
+}
+
+// The filter of a decimated row pair of length 3N in place: forward DFT,
+// x H(f)/3N (the filter table), inverse DFT (unnormalised, the 1/3N is in
+// the table). Ends with the sequence's barrier.
+template <int N>
+__device__ __forceinline__ void filter_rows3(float2* buf, int LB, const float2* __restrict__ twN,
+                                             const float2* __restrict__ tw3N, const float* __restrict__ filt,
+                                             int t96, int lane, int seq) {
+    const int w3 = t96 >> 5;
+    fft_warp<N>(buf + w3 * LB, twN, -1.f, lane);
+    seq_sync(seq);
+    for (int k = t96; k < N; k += 96) {
+        float2 y[3] = {buf[k], buf[LB + k], buf[2 * LB + k]};
+        const float2 w1 = __ldg(tw3N + k), w2 = __ldg(tw3N + 2 * k);
+        y[1] = cmul(y[1], w1);
+        y[2] = cmul(y[2], w2);
+        bfly<3>(y, -1.f);                         // X[k + N j], j = 0, 1, 2
+#pragma unroll
+        for (int j = 0; j < 3; ++j) y[j] = cscale(y[j], __ldg(filt + k + N * j));
+        bfly<3>(y, +1.f);                         // inverse radix-3 step
+        y[1] = cmul(y[1], make_float2(w1.x, -w1.y));
+        y[2] = cmul(y[2], make_float2(w2.x, -w2.y));
+        buf[k] = y[0];
+        buf[LB + k] = y[1];
+        buf[2 * LB + k] = y[2];
+    }
+    seq_sync(seq);
+    fft_warp<N>(buf + w3 * LB, twN, +1.f, lane);
+    seq_sync(seq);
+}
+
+// Filter (direct form) for Wp = 3N: a block holds blockDim/96 row pairs.
+template <int N, typename Tin>
+__global__ void __launch_bounds__(384) k_filter3(const Tin* __restrict__ d, float* __restrict__ q, long row0,
+                                                 long row1, int W, const float2* __restrict__ twN,
+                                                 const float2* __restrict__ tw3N, const float* __restrict__ filt) {
+    extern __shared__ float2 sm[];
+    const int seq = threadIdx.x / 96, t96 = threadIdx.x % 96, lane = threadIdx.x & 31;
+    const long rA = row0 + 2 * ((long)blockIdx.x * (blockDim.x / 96) + seq);
+    if (rA >= row1) return;                       // the whole sequence leaves: no barrier waits on it
+    const bool hasB = rA + 1 < row1;
+    float2* buf = sm + (size_t)seq * 3 * N;
+    load_rows3(d, buf, N, N, rA, hasB, W, 0, t96);
+    seq_sync(seq);
+    filter_rows3<N>(buf, N, twN, tw3N, filt, t96, lane, seq);
+    for (int j = t96; j < W; j += 96) {
+        const float2 v = buf[(j % 3) * N + j / 3];
+        q[(size_t)rA * W + j] = v.x;
+        if (hasB) q[(size_t)(rA + 1) * W + j] = v.y;
+    }
+}
+
+// Fourier row pass for Wf = 3 NF (NF = 256 or 512), optionally after the
+// filter (N > 0: Wp = 3N, NF <= N, offu a multiple of 3): the filtered row
+// stays decimated, and since offu = 3 o, the decimated subsequences of the
+// padded row are the filter's buffers shifted by o slots (zero past W). Then
+// the NF-point warp FFTs, the radix-3 step written back in natural order
+// (X[k + NF j] in buffer j, slot k), and the same epilogue as k_rowfft: the
+// two real spectra, the centring phase, R[row][m + Wf/2].
+template <int N, int NF, typename Tin>
+__global__ void __launch_bounds__(384) k_rowfft3(const Tin* __restrict__ d, float2* __restrict__ R,
+                                                 long row0, long row1, int W, int offu,
+                                                 const float2* __restrict__ twN, const float2* __restrict__ tw3N,
+                                                 const float* __restrict__ filt,
+                                                 const float2* __restrict__ twNF, const float2* __restrict__ tw3NF,
+                                                 const float2* __restrict__ phu) {
+    extern __shared__ float2 sm[];
+    constexpr int LB = (N > NF) ? N : NF;
+    const int seq = threadIdx.x / 96, t96 = threadIdx.x % 96, lane = threadIdx.x & 31, w3 = t96 >> 5;
+    const long rA = row0 + 2 * ((long)blockIdx.x * (blockDim.x / 96) + seq);
+    if (rA >= row1) return;
+    const bool hasB = rA + 1 < row1;
+    float2* buf = sm + (size_t)seq * 3 * LB;
+    if constexpr (N > 0) {
+        load_rows3(d, buf, LB, N, rA, hasB, W, 0, t96);
+        seq_sync(seq);
+        filter_rows3<N>(buf, LB, twN, tw3N, filt, t96, lane, seq);
+        // shift buffer w3 by o = offu/3 slots, zero past the row (each warp its own buffer)
+        const int o = offu / 3;
+        float2 v[NF / 32];
+        float2* bw = buf + w3 * LB;
+#pragma unroll
+        for (int i = 0; i < NF / 32; ++i) {
+            const int a = lane + 32 * i, src = a - o, j = 3 * src + w3;
+            v[i] = (src >= 0 && j < W) ? bw[src] : make_float2(0.f, 0.f);
+        }
+        __syncwarp();
+#pragma unroll
+        for (int i = 0; i < NF / 32; ++i) bw[lane + 32 * i] = v[i];
+        __syncwarp();
+    } else {
+        load_rows3(d, buf, LB, NF, rA, hasB, W, offu, t96);
+        seq_sync(seq);
+    }
+    fft_warp<NF>(buf + w3 * LB, twNF, -1.f, lane);
+    seq_sync(seq);
+    for (int k = t96; k < NF; k += 96) {
+        float2 y[3] = {buf[k], buf[LB + k], buf[2 * LB + k]};
+        y[1] = cmul(y[1], __ldg(tw3NF + k));
+        y[2] = cmul(y[2], __ldg(tw3NF + 2 * k));
+        bfly<3>(y, -1.f);
+        buf[k] = y[0];
+        buf[LB + k] = y[1];
+        buf[2 * LB + k] = y[2];
+    }
+    seq_sync(seq);
+    constexpr int Nf = 3 * NF, half = Nf / 2;
+    auto X = [&](int i) { return buf[(i / NF) * LB + i % NF]; };
+    for (int mi = t96; mi < Nf; mi += 96) {
+        const int m = mi - half;
+        const int i1 = m < 0 ? m + Nf : m;          // index of +m
+        const int i2 = m > 0 ? Nf - m : -m;         // index of -m
+        float2 Z = X(i1), Zc = X(i2);
+        Zc.y = -Zc.y;
+        const float2 A = make_float2(0.5f * (Z.x + Zc.x), 0.5f * (Z.y + Zc.y));
+        const float2 Dm = csub(Z, Zc);
+        const float2 B = make_float2(0.5f * Dm.y, -0.5f * Dm.x);   // (Z - conj Z(-m)) / (2i)
+        const float2 ph = __ldg(phu + mi);
+        R[(size_t)rA * Nf + mi] = cmul(A, ph);
+        if (hasB) R[(size_t)(rA + 1) * Nf + mi] = cmul(B, ph);
+    }
+}
+
 // Row pairs per block: blocks of about 128 threads (one pair for rows of
 // 1024 or more): small blocks wait on fewer warps at each FFT barrier and
 // more of them share an SM.
@@ -145,6 +307,23 @@ int filter_typed(lamino_plan_t p, const Tin* d, float* q, int kind, cudaStream_t
     const FftDesc& f = p->fWp;
     long npairs = (row1 - row0 + 1) / 2;
     if (npairs <= 0) return LAMINO_OK;
+    const float* filt3 = p->d_filt + (size_t)kind * p->Wp;
+    if (p->fWp3.n == 512 || p->fWp3.n == 256) {
+        // three one-warp transforms per row pair, four row pairs per block
+        const int N = p->fWp3.n;
+        const size_t smem = sizeof(float2) * 3 * N * 4;
+        dim3 grid((unsigned)((npairs + 3) / 4));
+        ProfScope prof(p, "filter", s);
+        if (N == 512) {
+            cudaFuncSetAttribute(k_filter3<512, Tin>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+            k_filter3<512, Tin><<<grid, 384, smem, s>>>(d, q, row0, row1, p->W, p->fWp3.tw, f.tw, filt3);
+        } else {
+            cudaFuncSetAttribute(k_filter3<256, Tin>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+            k_filter3<256, Tin><<<grid, 384, smem, s>>>(d, q, row0, row1, p->W, p->fWp3.tw, f.tw, filt3);
+        }
+        LAM_LAUNCH_CHECK(p, "filter kernel");
+        return LAMINO_OK;
+    }
     int pairs = pairs_for(f.t, sizeof(float2) * fpad_len(f.n));
     size_t smem = sizeof(float2) * fpad_len(f.n) * pairs;
     dim3 grid((unsigned)((npairs + pairs - 1) / pairs));
@@ -181,10 +360,49 @@ int rowfft_launch(lamino_plan_t p, const Tin* d, float2* R, const float* filt, c
     return LAMINO_OK;
 }
 
+template <int N, int NF, typename Tin>
+int rowfft3_launch(lamino_plan_t p, const Tin* d, float2* R, const float* filt, cudaStream_t s,
+                   long row0, long row1) {
+    long npairs = (row1 - row0 + 1) / 2;
+    if (npairs <= 0) return LAMINO_OK;
+    constexpr int LB = (N > NF) ? N : NF;
+    const size_t smem = sizeof(float2) * 3 * LB * 4;
+    dim3 grid((unsigned)((npairs + 3) / 4));
+    auto kern = k_rowfft3<N, NF, Tin>;
+    cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    ProfScope prof(p, N > 0 ? "filter_rowfft" : "rowfft", s);
+    kern<<<grid, 384, smem, s>>>(d, R, row0, row1, p->W, p->offu, N > 0 ? p->fWp3.tw : nullptr,
+                                 N > 0 ? p->fWp.tw : nullptr, filt, p->fWf3.tw, p->fWf.tw, p->d_phu);
+    LAM_LAUNCH_CHECK(p, "row FFT kernel");
+    return LAMINO_OK;
+}
+
+// The decimated-by-3 row kernels apply when the lengths are 3 x (256 or 512)
+// and, after the filter, the row offset in the padded Fourier row is a
+// multiple of 3 with the Fourier length not above the filter's.
+template <typename Tin>
+int rowfft3_typed(lamino_plan_t p, const Tin* d, float2* R, const float* filt, cudaStream_t s, long r0,
+                  long r1, bool* done) {
+    *done = false;
+    const int nf = p->fWf3.n, np = filt ? p->fWp3.n : 0;
+    const bool nf_ok = nf == 256 || nf == 512;
+    if (!nf_ok) return LAMINO_OK;
+    if (filt && !((np == 256 || np == 512) && nf <= np && p->offu % 3 == 0)) return LAMINO_OK;
+    *done = true;
+    if (!filt) return nf == 256 ? rowfft3_launch<0, 256, Tin>(p, d, R, filt, s, r0, r1)
+                                : rowfft3_launch<0, 512, Tin>(p, d, R, filt, s, r0, r1);
+    if (np == 512) return nf == 256 ? rowfft3_launch<512, 256, Tin>(p, d, R, filt, s, r0, r1)
+                                    : rowfft3_launch<512, 512, Tin>(p, d, R, filt, s, r0, r1);
+    return rowfft3_launch<256, 256, Tin>(p, d, R, filt, s, r0, r1);
+}
+
 template <typename Tin>
 int rowfft_typed(lamino_plan_t p, const Tin* d, float2* R, int kind, cudaStream_t s, long r0,
                  long r1) {
     const float* filt = kind >= 0 ? p->d_filt + (size_t)kind * p->Wp : nullptr;
+    bool done = false;
+    int rc3 = rowfft3_typed(p, d, R, filt, s, r0, r1, &done);
+    if (done) return rc3;
     const int ef = p->fWf.e;
     if (kind < 0) {
         return ef == 8 ? rowfft_launch<0, 8, Tin>(p, d, R, filt, s, r0, r1)

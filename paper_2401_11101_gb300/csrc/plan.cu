@@ -286,6 +286,9 @@ int build_tables(lamino_plan_t p) {
 
     // FFT twiddles exp(-2 pi i s/n) of every length in use, computed in double
     std::vector<int> lens = {p->Wp, p->Wf, p->Hf, p->M1, p->M2, p->M3};
+    // the decimated-by-3 row kernels use 256- and 512-point tables for Wp, Wf = 3 x 256 or 3 x 512
+    for (int n : {p->Wp, p->Wf})
+        if (n % 3 == 0 && (n / 3 == 256 || n / 3 == 512)) lens.push_back(n / 3);
     std::vector<int> uniq;
     for (int n : lens)
         if (fft_len_ok(n) && std::find(uniq.begin(), uniq.end(), n) == uniq.end()) uniq.push_back(n);
@@ -312,6 +315,8 @@ int build_tables(lamino_plan_t p) {
     p->fM1 = desc_for(p->M1);
     p->fM2 = desc_for(p->M2);
     p->fM3 = desc_for(p->M3);
+    p->fWp3 = (p->Wp % 3 == 0 && (p->Wp / 3 == 256 || p->Wp / 3 == 512)) ? desc_for(p->Wp / 3) : FftDesc();
+    p->fWf3 = (p->Wf % 3 == 0 && (p->Wf / 3 == 256 || p->Wf / 3 == 512)) ? desc_for(p->Wf / 3) : FftDesc();
 
     // centring phases: data sit at padded column j' = j + offu, so the type-1 sum
     // carries exp(2 pi i m cu / Wf), cu = W/2 + offu (and likewise for rows);
@@ -411,16 +416,53 @@ int validate_dtype_kind(lamino_plan_t p, int dtype, int kind) {
     return LAMINO_OK;
 }
 
-// Allocates (or keeps) the plan's two Fourier workspaces for its current
-// z chunking and returns their views.
+// The plan's two Fourier workspaces for its current z chunking: views of the
+// caller's lent buffer (A at 0, B 256-byte aligned after it), or plan-owned
+// buffers allocated (or kept) here.
 int fourier_buffers(lamino_plan_t p, FourierBufs* fb) {
     size_t a, b;
     fourier_workspace(p, &a, &b);
+    if (p->lent) {
+        const size_t need = lent_align(a) + b;
+        if (need > p->lent_bytes)
+            return fail(p, LAMINO_ENOMEM, "the lent workspace holds %zu bytes; the Fourier form needs %zu",
+                        p->lent_bytes, need);
+        *fb = fourier_bufs(p, p->lent, static_cast<char*>(p->lent) + lent_align(a));
+        return LAMINO_OK;
+    }
     int rc = ensure_buffer(p, &p->ws_a, &p->ws_a_bytes, a, "Fourier workspace A");
     if (rc) return rc;
     if ((rc = ensure_buffer(p, &p->ws_b, &p->ws_b_bytes, b, "Fourier workspace B"))) return rc;
     *fb = fourier_bufs(p, p->ws_a, p->ws_b);
     return LAMINO_OK;
+}
+
+int rows_buffer(lamino_plan_t p, float** q) {
+    const size_t need = sizeof(float) * (size_t)p->nproj * p->H * p->W;
+    if (p->lent) {
+        if (need > p->lent_bytes)
+            return fail(p, LAMINO_ENOMEM, "the lent workspace holds %zu bytes; the filtered rows need %zu",
+                        p->lent_bytes, need);
+        *q = static_cast<float*>(p->lent);
+        return LAMINO_OK;
+    }
+    int rc = ensure_buffer(p, (void**)&p->q_buf, &p->q_buf_bytes, need, "filtered rows");
+    *q = p->q_buf;
+    return rc;
+}
+
+int pad_buffer(lamino_plan_t p, size_t need, float** q) {
+    if (p->lent) {
+        const size_t off = lent_align(sizeof(float) * (size_t)p->nproj * p->H * p->W);
+        if (off + need > p->lent_bytes)
+            return fail(p, LAMINO_ENOMEM, "the lent workspace holds %zu bytes; the padded projections "
+                        "need %zu", p->lent_bytes, off + need);
+        *q = reinterpret_cast<float*>(static_cast<char*>(p->lent) + off);
+        return LAMINO_OK;
+    }
+    int rc = ensure_buffer(p, (void**)&p->q_pad, &p->q_pad_bytes, need, "padded projections");
+    *q = p->q_pad;
+    return rc;
 }
 
 }  // namespace lam
@@ -596,10 +638,10 @@ int lamino_fbp(lamino_plan_t p, int form, const void* d, int dtype, float* vol, 
     if (form == LAMINO_FOURIER) return fourier_common(p, d, dtype, vol, kind, stream);
     if (form != LAMINO_DIRECT) return fail(p, LAMINO_EINVAL, "unknown form %d", form);
     if (!p->filter_ok) return fail(p, LAMINO_EUNSUPPORTED, "filter length %d is not a supported FFT length", p->Wp);
-    size_t need = sizeof(float) * (size_t)p->nproj * p->H * p->W;
-    if ((rc = ensure_buffer(p, (void**)&p->q_buf, &p->q_buf_bytes, need, "filtered rows"))) return rc;
-    if ((rc = launch_filter(p, d, dtype, p->q_buf, kind, stream))) return rc;
-    return launch_direct(p, p->q_buf, vol, stream);
+    float* qb = nullptr;
+    if ((rc = rows_buffer(p, &qb))) return rc;
+    if ((rc = launch_filter(p, d, dtype, qb, kind, stream))) return rc;
+    return launch_direct(p, qb, vol, stream);
 }
 
 // Host pipeline of lamino_fbp_host: the projections go up in chunks of whole
@@ -640,10 +682,9 @@ int lamino_fbp_host(lamino_plan_t p, int form, const void* d_host, int dtype, fl
     FourierBufs fb;
     if (form == LAMINO_FOURIER) {
         if ((rc = fourier_buffers(p, &fb))) return rc;
-    } else {
-        size_t need = sizeof(float) * (size_t)p->nproj * p->H * p->W;
-        if ((rc = ensure_buffer(p, (void**)&p->q_buf, &p->q_buf_bytes, need, "filtered rows"))) return rc;
     }
+    float* qb = nullptr;
+    if (form != LAMINO_FOURIER && (rc = rows_buffer(p, &qb))) return rc;
     const int nin = std::min(8, p->nproj);                          // projection chunks
     const int nout = form == LAMINO_FOURIER ? std::min(8, p->n1) : 1;   // volume slabs
     if ((rc = ensure_pipeline(p, (size_t)nin + nout + 2))) return rc;
@@ -667,7 +708,7 @@ int lamino_fbp_host(lamino_plan_t p, int form, const void* d_host, int dtype, fl
                 return rc;
             if ((rc = launch_colfft(p, fb, (int)k0, (int)k1, stream))) return rc;
         } else {
-            if ((rc = launch_filter(p, p->h_in, dtype, p->q_buf, kind, stream, k0 * p->H, k1 * p->H)))
+            if ((rc = launch_filter(p, p->h_in, dtype, qb, kind, stream, k0 * p->H, k1 * p->H)))
                 return rc;
         }
     }
@@ -685,7 +726,7 @@ int lamino_fbp_host(lamino_plan_t p, int form, const void* d_host, int dtype, fl
                                           slice, (i11 - i10) * row, p->n2, cudaMemcpyDeviceToHost, cs));
         }
     } else {
-        if ((rc = launch_direct(p, p->q_buf, p->h_vol, stream))) return rc;
+        if ((rc = launch_direct(p, qb, p->h_vol, stream))) return rc;
         LAM_CUDA(p, cudaEventRecord(evo[0], stream));
         LAM_CUDA(p, cudaStreamWaitEvent(cs, evo[0], 0));
         LAM_CUDA(p, cudaMemcpyAsync(vol_host, p->h_vol, dvol, cudaMemcpyDeviceToHost, cs));
@@ -718,6 +759,28 @@ int lamino_device_bytes(lamino_plan_t p, size_t* bytes) {
     return LAMINO_OK;
 }
 
+int lamino_set_workspace(lamino_plan_t p, void* ws, size_t bytes) {
+    if (!p) return fail(nullptr, LAMINO_EINVAL, "NULL plan");
+    if ((ws == nullptr) != (bytes == 0))
+        return fail(p, LAMINO_EINVAL, "lamino_set_workspace: pointer and size must both be set or both be 0");
+    if ((uintptr_t)ws % 256)
+        return fail(p, LAMINO_EINVAL, "lamino_set_workspace: the buffer must be 256-byte aligned");
+    int rc = set_device(p);
+    if (rc) return rc;
+    if (ws && (p->ws_a || p->ws_b || p->q_buf || p->q_pad)) {
+        // the plan's own workspaces are no longer used; cudaFree waits for the device
+        void* own[] = {p->ws_a, p->ws_b, p->q_buf, p->q_pad};
+        for (void* b : own)
+            if (b) LAM_CUDA(p, cudaFree(b));
+        p->ws_a = p->ws_b = nullptr;
+        p->q_buf = p->q_pad = nullptr;
+        p->ws_a_bytes = p->ws_b_bytes = p->q_buf_bytes = p->q_pad_bytes = 0;
+    }
+    p->lent = ws;
+    p->lent_bytes = bytes;
+    return LAMINO_OK;
+}
+
 int lamino_set_z_chunk(lamino_plan_t p, int z_chunk) {
     if (!p) return fail(nullptr, LAMINO_EINVAL, "NULL plan");
     if (z_chunk < 0) return fail(p, LAMINO_EINVAL, "z_chunk must be >= 0, not %d", z_chunk);
@@ -743,8 +806,8 @@ int lamino_workspace_bytes(lamino_plan_t p, int form, size_t* bytes) {
     } else if (form == LAMINO_DIRECT) {
         *bytes = sizeof(float) * (size_t)p->nproj * p->H * p->W;
         // rows whose width is not a multiple of 4 floats are staged at a
-        // 16-byte pitch for the TMA loads
-        if (p->W % 4) *bytes += sizeof(float) * (size_t)p->nproj * p->H * ((p->W + 3) / 4 * 4);
+        // 16-byte pitch for the TMA loads (after the filtered rows, aligned)
+        if (p->W % 4) *bytes = lent_align(*bytes) + sizeof(float) * (size_t)p->nproj * p->H * ((p->W + 3) / 4 * 4);
     } else {
         return fail(p, LAMINO_EINVAL, "unknown form %d", form);
     }

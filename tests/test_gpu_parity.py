@@ -77,6 +77,44 @@ def test_filter_ragged_rows(L):
     assert np.abs(q - ref).max() / np.abs(ref).max() < 1e-5
 
 
+@pytest.mark.parametrize("geom", [
+    I.Geometry(32, 32, 8, 6, 12, 768, math.radians(20.0)),    # Wp = 3x512, Wf = 3x256, offset 0
+    I.Geometry(32, 32, 8, 6, 12, 762, math.radians(20.0)),    # Wf = 3x256, offset 3 (shifted buffers)
+    I.Geometry(32, 32, 8, 5, 11, 384, math.radians(20.0)),    # Wp = 3x256, odd row count
+    I.Geometry(32, 32, 8, 5, 11, 1500, math.radians(20.0)),   # Wf = 3x512 (row pass without filter)
+    I.Geometry(384, 384, 4, 4, 8, 300, math.radians(20.0)),   # Wp = Wf = 3x256, offset 234
+    I.Geometry(800, 800, 2, 3, 4, 702, math.radians(20.0)),   # Wp = Wf = 3x512, offset 417
+])
+def test_row_kernels_3x_parity(L, geom):
+    # the decimated-by-3 row kernels (three one-warp transforms per row pair)
+    # against the oracle: filter, Fourier row pass with and without the fused
+    # filter, and the direct FBP behind the filter
+    d = torch.as_tensor(I.random_projections(geom, 31), dtype=torch.float32)
+    # columns within 4 voxels of the rotation axis: they project onto the
+    # detector at every angle even where it has only a few rows
+    rng = np.random.default_rng(32)
+    cols = np.stack([geom.n0 // 2 + rng.integers(-4, 4, 6), geom.n1 // 2 + rng.integers(-4, 4, 6)],
+                    axis=1).astype(np.int32)
+    with plan_for(L, geom) as p:
+        info = p.info
+        q = p.filter(d.cuda(), "shepp").cpu().numpy()
+        vf = p.fbp(d.cuda(), form="fourier", kind="shepp").cpu().numpy()
+        vd = p.fbp(d.cuda(), form="direct", kind="shepp").cpu().numpy()
+        vb = p.backproject_fourier(d.cuda()).cpu().numpy()
+        p.status()
+    qo = O.filter_rows(d.numpy(), geom, "shepp")
+    ef = np.abs(q - qo).max() / np.abs(qo).max()
+    pick = lambda v: np.stack([v[:, i1, i0] for i0, i1 in cols])
+    e_fbp = rel(pick(vf), O.backproject_trig_columns(qo, geom, cols))
+    e_dir = rel(pick(vd), O.backproject_direct_columns(qo, geom, cols))
+    e_bp = rel(pick(vb), O.backproject_trig_columns(d.numpy(), geom, cols))
+    print(f"{geom} Wp={info['wp']} Wf={info['wf']}: filter {ef:.1e}, Fourier FBP {e_fbp:.2e}, "
+          f"direct FBP {e_dir:.2e}, Fourier BP {e_bp:.2e}")
+    assert ef < 1e-5
+    assert e_fbp <= 1e-4 and e_bp <= 1e-4
+    assert e_dir <= 1e-5
+
+
 # ----------------------------------------------------------------- direct
 
 def test_direct_parity_c1(L):
