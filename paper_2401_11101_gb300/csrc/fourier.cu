@@ -93,6 +93,7 @@ struct GridArgs {
                                              // the launch (blockIdx.y = l - l0; V is [l - l0])
     int civ_cap;                             // entries of the group table (0: none)
     float sinphi, c1, c2;  // c = -1/(4t) per axis
+    float q1, q2;          // exp(2 c) per axis (gauss_taps)
     FftDesc f1;
 };
 
@@ -149,6 +150,24 @@ __device__ __forceinline__ int band_intervals(float A, float B, int mlo, int mhi
         }
     }
     return n;
+}
+
+// The 2W Gaussian weights exp(c (d0 + j)^2), j = 0 .. N-1, of one point along
+// one axis (d0 = offset of its first cell), by the factorisation of fast
+// Gaussian gridding (Greengard & Lee, SIAM Rev. 2004): the ratio of
+// consecutive weights is exp(c (2 (d0 + j) + 1)) = r0 q^j with q = exp(2c),
+// so two exponentials and two products per weight replace N exponentials.
+// Every weight and ratio stays within exp(+-c (2N)^2), far inside float range.
+template <int N>
+__device__ __forceinline__ void gauss_taps(float (&g)[N], float c, float q, float d0) {
+    float v = __expf(c * d0 * d0);
+    float r = __expf(c * fmaf(2.f, d0, 1.f));
+#pragma unroll
+    for (int j = 0; j < N; ++j) {
+        g[j] = v;
+        v *= r;
+        r *= q;
+    }
 }
 
 // Exclusive prefix sum of n ints in shared memory (in place), whole block;
@@ -398,11 +417,7 @@ __global__ void __launch_bounds__(1024, 1) k_grid(GridArgs a) {
         const float fx = floorf(X), fy = floorf(Y);
         float gx[2 * W];
         const int sx0 = (int)fx - W + 1;
-#pragma unroll
-        for (int c = 0; c < 2 * W; ++c) {
-            const float dx = fx - W + 1 + c - X;
-            gx[c] = __expf(a.c1 * dx * dx);
-        }
+        gauss_taps(gx, a.c1, a.q1, fx - W + 1 - X);
         const bool wraps = sx0 < 0 || sx0 + 2 * W > M1;   // rare: within W of the grid edge
         // rows of the point: s2 = fy - W + 1 + jy; band row rr = s2 - s20 (mod M2)
         int r0 = (int)fy - W + 1 - s20;                 // in (-2 M2 - W, M2)
@@ -410,11 +425,7 @@ __global__ void __launch_bounds__(1024, 1) k_grid(GridArgs a) {
         r0 += (r0 < 0) ? M2 : 0;
         r0 -= (r0 >= M2) ? M2 : 0;                      // now in [0, M2); 2W <= M2
         float gyv[2 * W];
-#pragma unroll
-        for (int jy = 0; jy < 2 * W; ++jy) {
-            const float dy = (float)((int)fy - W + 1 + jy) - Y;
-            gyv[jy] = __expf(a.c2 * dy * dy);
-        }
+        gauss_taps(gyv, a.c2, a.q2, fy - W + 1 - Y);
 #pragma unroll
         for (int jy = 0; jy < 2 * W; ++jy) {
             int rr = r0 + jy;
@@ -681,13 +692,13 @@ __global__ void __launch_bounds__(512, 1) k_grid_t(GridArgs a, const float2* __r
         r0 += (r0 < 0) ? M2 : 0;
         r0 -= (r0 >= M2) ? M2 : 0;
         if (r0 >= T2) continue;                 // owned by another band
-        float gx[2 * W];
+        float gx[2 * W], gyv[2 * W];
         int col[2 * W];
         const int sx0 = (int)fx - W + 1;
+        gauss_taps(gx, a.c1, a.q1, fx - W + 1 - X0);
+        gauss_taps(gyv, a.c2, a.q2, fy - W + 1 - Y);
 #pragma unroll
         for (int c = 0; c < 2 * W; ++c) {
-            const float dx = fx - W + 1 + c - X0;
-            gx[c] = __expf(a.c1 * dx * dx);
             int s1 = sx0 + c;
             s1 += (s1 < 0) ? M1 : 0;
             s1 -= (s1 >= M1) ? M1 : 0;
@@ -696,8 +707,7 @@ __global__ void __launch_bounds__(512, 1) k_grid_t(GridArgs a, const float2* __r
         float2 acc = make_float2(0.f, 0.f);
 #pragma unroll
         for (int jy = 0; jy < 2 * W; ++jy) {
-            const float dy = (float)((int)fy - W + 1 + jy) - Y;
-            const float gy = __expf(a.c2 * dy * dy);
+            const float gy = gyv[jy];
             const float2* row = X + (size_t)(r0 + jy) * ld;
             float2 racc = make_float2(0.f, 0.f);
 #pragma unroll
@@ -877,6 +887,8 @@ static GridArgs grid_args(lamino_plan_t p) {
     a.sinphi = (float)sin(p->tilt);
     a.c1 = (float)(-1.0 / (4.0 * p->t1));
     a.c2 = (float)(-1.0 / (4.0 * p->t2));
+    a.q1 = (float)exp(-2.0 / (4.0 * p->t1));
+    a.q2 = (float)exp(-2.0 / (4.0 * p->t2));
     a.f1 = p->fM1;
     return a;
 }
