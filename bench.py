@@ -308,6 +308,7 @@ def run_serving(n: int, rate: float, device: int, seed: int = 5) -> dict:
     rep = srv.stop()
     out = rep.summary(reqs)
     out.update({"rate_req_s": rate, "slots": 4, "form": "fourier", "input_generation_s": gen_s,
+                "budget_gb": srv.budget / 1e9,
                 "mode": "live: a client thread submits at Poisson arrival times while the loop thread runs",
                 "workload": "mixed volumes {128^3, 256^2x128, 512^2x256, 1024^2x256}, "
                             "180-1800 angles, tilt U[10,40] deg, det 1.5 n0 x n2, FP16"})

@@ -274,6 +274,24 @@ int lamino_workspace_bytes(lamino_plan_t plan, int form, size_t* bytes);
 int lamino_device_bytes(lamino_plan_t plan, size_t* bytes);
 
 /*
+ * lamino_set_workspace -- lend the plan a caller-owned device buffer for its
+ * workspaces (the role of a work area set on an FFT plan): from now on the
+ * Fourier form's two workspaces, and the direct form's filtered rows and
+ * 16-byte-pitch copy, are views of `ws` instead of plan-owned allocations, so
+ * the calls allocate no workspace (lamino_fbp_host still owns its device copies
+ * of the host data). `bytes` must cover lamino_workspace_bytes of the form
+ * used, else that call fails with LAMINO_ENOMEM and a message giving both
+ * sizes. `ws` must be 256-byte aligned, must stay valid, and must not be used
+ * for anything else while calls of this plan that use it are in flight (one
+ * buffer can serve many plans whose calls are serialised, e.g. on one stream).
+ * Workspaces the plan had allocated itself are freed (which waits for the
+ * device). ws = NULL with bytes = 0 returns to plan-owned workspaces,
+ * allocated on the next use. Errors: EINVAL (misaligned, or one of ws/bytes
+ * zero), ECUDA.
+ */
+int lamino_set_workspace(lamino_plan_t plan, void* ws, size_t bytes);
+
+/*
  * lamino_set_z_chunk -- change the z chunking of a plan (see lamino_opts.z_chunk;
  * Sec. 5, chunking by slices and columns). Frees the plan's Fourier workspaces
  * (which waits for the device); the next call allocates them for the new

@@ -332,12 +332,13 @@ int launch_direct(lamino_plan_t p, const float* q, float* vol, cudaStream_t s) {
     if ((p->W % 4) || ((uintptr_t)q % 16)) {
         pitch = (p->W + 3) / 4 * 4;
         size_t need = sizeof(float) * (size_t)p->nproj * p->H * pitch;
-        int rc = ensure_buffer(p, (void**)&p->q_pad, &p->q_pad_bytes, need, "padded projections");
+        float* qp = nullptr;
+        int rc = pad_buffer(p, need, &qp);
         if (rc) return rc;
-        LAM_CUDA(p, cudaMemsetAsync(p->q_pad, 0, need, s));
-        LAM_CUDA(p, cudaMemcpy2DAsync(p->q_pad, sizeof(float) * pitch, q, sizeof(float) * p->W,
+        LAM_CUDA(p, cudaMemsetAsync(qp, 0, need, s));
+        LAM_CUDA(p, cudaMemcpy2DAsync(qp, sizeof(float) * pitch, q, sizeof(float) * p->W,
                                       sizeof(float) * p->W, (size_t)p->nproj * p->H, cudaMemcpyDeviceToDevice, s));
-        src = p->q_pad;
+        src = qp;
     }
     PFN_cuTensorMapEncodeTiled_v12000 encode = get_encode();
     if (!encode) return fail(p, LAMINO_ECUDA, "cuTensorMapEncodeTiled is not available from the driver");

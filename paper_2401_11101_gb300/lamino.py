@@ -31,7 +31,7 @@ FORMS = {"direct": DIRECT, "fourier": FOURIER}
 EXPORTS = ("lamino_plan", "lamino_get_info", "lamino_filter", "lamino_backproject_direct",
            "lamino_backproject_fourier", "lamino_backproject_fourier_noalloc", "lamino_fbp", "lamino_fbp_host", "lamino_project",
            "lamino_status", "lamino_selftest_wait", "lamino_profile", "lamino_profile_read", "lamino_workspace_bytes",
-           "lamino_set_z_chunk", "lamino_device_bytes",
+           "lamino_set_z_chunk", "lamino_device_bytes", "lamino_set_workspace",
            "lamino_last_error", "lamino_destroy")
 
 
@@ -87,6 +87,7 @@ def load_library(path: str = LIB_PATH):
     lib.lamino_workspace_bytes.argtypes = [vp, ci, ctypes.POINTER(sz)]
     lib.lamino_set_z_chunk.argtypes = [vp, ci]
     lib.lamino_device_bytes.argtypes = [vp, ctypes.POINTER(sz)]
+    lib.lamino_set_workspace.argtypes = [vp, vp, sz]
     lib.lamino_profile.argtypes = [vp, ci]
     lib.lamino_profile_read.argtypes = [vp, ctypes.POINTER(_KTime), ci, ctypes.POINTER(ci)]
     lib.lamino_last_error.argtypes = [vp]
@@ -238,6 +239,21 @@ class Plan:
         self._check(self._lib.lamino_project(self._h, _form(form), vol.data_ptr(), d.data_ptr(),
                                              _stream(self.device)))
         return d
+
+    def set_workspace(self, buf):
+        """Lend a CUDA tensor (any dtype, contiguous, 256-byte aligned) as this
+        plan's workspace, or None to return to plan-owned workspaces. The plan
+        keeps a reference while it is lent."""
+        if buf is None:
+            self._check(self._lib.lamino_set_workspace(self._h, None, 0))
+            self._lent = None
+            return
+        if not isinstance(buf, torch.Tensor) or not buf.is_cuda or buf.device != self.device \
+                or not buf.is_contiguous():
+            raise ValueError("workspace must be a contiguous CUDA tensor on the plan's device")
+        self._check(self._lib.lamino_set_workspace(self._h, buf.data_ptr(),
+                                                   buf.numel() * buf.element_size()))
+        self._lent = buf
 
     def set_z_chunk(self, z_chunk: int):
         """k_v planes per Fourier chunk / slices per direct launch (0: none);

@@ -7,13 +7,18 @@ form's workspace from lamino_workspace_bytes + input + output), backfilling
 past a request that does not fit yet. Admitted requests run concurrently on
 their slot streams, so the kernels of different requests overlap on the GPU.
 
-Plans (with their device tables and workspaces) stay resident in a pool keyed
-by geometry after their request finishes. Their device bytes count against
-the budget too: when a request would not fit, idle plans are closed least
-recently used first (never the one the request is about to reuse), and the
-pool is capped in size. A request in form "auto" runs the Fourier form,
-z-chunked (Sec. 5: k_v-plane chunks of the 2D USFFT) as finely as needed to
-fit the budget, and falls back to the direct form only if no chunking fits.
+Each slot owns a workspace arena that it lends to the plan it runs
+(lamino_set_workspace), so plans allocate no workspace of their own: plans
+(device tables only) stay resident in a pool keyed by geometry after their
+request finishes, and an arena grows only when a larger request comes. Idle
+plans and the arenas of idle slots count against the budget: when a request
+would not fit, idle plans are closed least recently used first (never the one
+the request is about to reuse), then idle arenas are released, and the pool is
+capped in size. Apart from closing a plan, nothing in the loop frees device
+memory or waits for the whole device. A request in form "auto" runs the
+Fourier form, z-chunked (Sec. 5: k_v-plane chunks of the 2D USFFT) as finely
+as needed to fit the budget, and falls back to the direct form only if no
+chunking fits.
 
 Completion is detected by polling CUDA events. A request that does not finish
 within `timeout_s` is reported as timed out at once, but its slot and its
@@ -324,21 +329,23 @@ class CudaBackend:
     """Runs requests with liblamino on one GPU, one CUDA stream per slot.
 
     Plans stay in an idle pool (LRU, at most `max_idle_plans`) between
-    requests. With `keep_volumes` every result is copied into its own pinned
-    host tensor; otherwise into a pinned buffer owned by the request's slot,
-    valid until that slot's next request."""
+    requests; their workspaces are the slots' arenas. With `keep_volumes` every
+    result is copied into its own pinned host tensor; otherwise into a pinned
+    buffer owned by the request's slot, valid until that slot's next request."""
 
     def __init__(self, device: int = 0, slots: int = 4, keep_volumes: bool = True,
-                 max_idle_plans: int = 16):
+                 max_idle_plans: int = 1024):
         import torch
         from . import lamino as L
         self.torch, self.L = torch, L
         self.device = torch.device("cuda", device)
         self.streams = [torch.cuda.Stream(device=self.device) for _ in range(slots)]
-        self.idle = collections.OrderedDict()     # (key, z_chunk) -> [Plan] (LRU order)
+        self.idle = collections.OrderedDict()     # geometry key -> [Plan] (LRU order)
         self.keep_volumes = keep_volumes
         self.max_idle_plans = max_idle_plans
         self.slot_out = [None] * slots
+        self.arena = [None] * slots                # per-slot workspace lent to the running plan
+        self.busy_slots = set()
         self.budget = None                         # set by the Server
         self._ws = {}
         self._planes = {}
@@ -370,26 +377,38 @@ class CudaBackend:
         still = []
         for h in self.draining:
             if h["ev"].query():
-                self._to_idle(h["pkey"], h["plan"])
+                self._idle_plan(h)
             else:
                 still.append(h)
         self.draining = still
 
+    def _new_plan(self, r: Request):
+        with self.torch.cuda.device(self.device):
+            return self.L.Plan(r.n0, r.n1, r.n2, r.nproj, r.det_w, r.det_h, r.tilt)
+
     def _plan(self, r: Request, zc: int):
+        """An idle plan of r's geometry (or a new one) set to z chunking zc;
+        plans hold no workspace (the slots lend theirs), so the chunking
+        changes without freeing anything."""
         self._drain()
-        pk = (r.key, zc)
-        lst = self.idle.get(pk)
+        lst = self.idle.get(r.key)
         if lst:
             p = lst.pop()
             if not lst:
-                del self.idle[pk]
-            return p
-        with self.torch.cuda.device(self.device):
-            return self.L.Plan(r.n0, r.n1, r.n2, r.nproj, r.det_w, r.det_h, r.tilt, z_chunk=zc)
+                del self.idle[r.key]
+        else:
+            p = self._new_plan(r)
+        if p.info["z_chunk"] != zc:
+            p.set_z_chunk(zc)
+        return p
+
+    def _idle_arenas(self) -> int:
+        return sum(a.numel() for i, a in enumerate(self.arena) if a is not None and i not in self.busy_slots)
 
     def idle_bytes(self, r: Request | None = None) -> int:
-        """Device bytes held by idle plans, not counting one plan that `r` would reuse."""
-        keep = (r.key, self.form_of(r)[1]) if r is not None else None
+        """Device bytes held by idle plans (not counting one plan that `r` would
+        reuse) and by the arenas of idle slots."""
+        keep = r.key if r is not None else None
         total, skipped = 0, False
         for pk, lst in self.idle.items():
             for p in lst:
@@ -397,35 +416,41 @@ class CudaBackend:
                     skipped = True
                     continue
                 total += p.device_bytes()
-        return total
+        return total + self._idle_arenas()
 
     def evict(self, target_idle: int, r: Request | None = None):
-        """Close idle plans, least recently used first, until their bytes
-        (without the one `r` would reuse) are at most `target_idle`."""
-        keep = (r.key, self.form_of(r)[1]) if r is not None else None
+        """Close idle plans, least recently used first, then release the arenas
+        of idle slots, until the idle bytes (without the plan `r` would reuse)
+        are at most `target_idle`."""
+        keep = r.key if r is not None else None
         while self.idle and self.idle_bytes(r) > max(0, target_idle):
             if not self._close_lru(keep):
                 break
+        for i in sorted(range(len(self.arena)), key=lambda i: -(self.arena[i].numel() if self.arena[i] is not None else 0)):
+            if self.idle_bytes(r) <= max(0, target_idle):
+                break
+            if i not in self.busy_slots:
+                self.arena[i] = None
 
     # ------------------------------------------------------------ footprints
-    def _probe(self, r: Request):
-        with self.torch.cuda.device(self.device):
-            return self.L.Plan(r.n0, r.n1, r.n2, r.nproj, r.det_w, r.det_h, r.tilt)
-
     def _form_bytes(self, r: Request, form: str, zc: int = 0) -> int:
-        """Footprint of r in one form: workspace + input + filtered/output buffers."""
+        """Footprint of r in one form: plan tables + workspace + input + output.
+        The plan that answers joins the idle pool for r to use (creating and
+        closing a plan here would wait for the whole device)."""
         esz = 2 if r.d is None else r.d.element_size()
         key = (r.key, form, zc, esz)
         if key not in self._ws:
-            p = self._probe(r)               # never runs: no workspace is allocated
-            try:
-                p.set_z_chunk(zc)
-                ws = p.workspace_bytes(form)
-                self._planes[r.key] = p.info["planes"]
-                tables = p.device_bytes()
-            finally:
-                p.close()
-            self._ws[key] = tables + ws + r.nproj * r.det_h * r.det_w * (esz + 4) + 4 * r.nvox
+            lst = self.idle.get(r.key)
+            p = lst[-1] if lst else None
+            if p is None:
+                p = self._new_plan(r)
+                self._to_idle(r.key, p)
+            keep = p.info["z_chunk"]
+            p.set_z_chunk(zc)                # no workspace is held: nothing is freed
+            ws = p.workspace_bytes(form)
+            p.set_z_chunk(keep)
+            self._planes[r.key] = p.info["planes"]
+            self._ws[key] = p.device_bytes() + ws + r.nproj * r.det_h * r.det_w * (esz + 4) + 4 * r.nvox
         return self._ws[key]
 
     def form_of(self, r: Request):
@@ -457,11 +482,24 @@ class CudaBackend:
             self.slot_out[slot] = buf
         return buf[:n].view(shape)
 
+    def _arena_for(self, slot: int, nbytes: int):
+        a = self.arena[slot]
+        if a is None or a.numel() < nbytes:
+            # the slot's previous request has finished (its slot was free): the old
+            # arena goes back to the allocator before the larger one is taken
+            self.arena[slot] = None
+            with self.torch.cuda.device(self.device), self.torch.cuda.stream(self.streams[slot]):
+                a = self.torch.empty(max(nbytes, 256), dtype=self.torch.uint8, device=self.device)
+            self.arena[slot] = a
+        return a
+
     def submit(self, r: Request, slot: int):
         torch = self.torch
         s = self.streams[slot]
         form, zc = self.form_of(r)
         p = self._plan(r, zc)
+        self.busy_slots.add(slot)
+        p.set_workspace(self._arena_for(slot, p.workspace_bytes(form)))
         with torch.cuda.device(self.device), torch.cuda.stream(s):
             d = r.d.to(self.device, non_blocking=True)
             vol = torch.empty(p.shape_vol, dtype=torch.float32, device=self.device)
@@ -473,8 +511,8 @@ class CudaBackend:
             host.copy_(vol, non_blocking=True)
             ev = torch.cuda.Event()
             ev.record(s)
-        return {"req": r, "plan": p, "pkey": (r.key, zc), "ev": ev, "d": d, "vol": vol, "host": host,
-                "stream": s, "form": form if not zc else f"{form}/z{zc}"}
+        return {"req": r, "plan": p, "pkey": r.key, "ev": ev, "d": d, "vol": vol, "host": host,
+                "stream": s, "slot": slot, "form": form if not zc else f"{form}/z{zc}"}
 
     def poll(self, h) -> bool:
         return h["ev"].query()
@@ -487,10 +525,16 @@ class CudaBackend:
         h["d"].record_stream(h["stream"])
         h["vol"].record_stream(h["stream"])
         if not h["ev"].query():
-            # work still in flight may use the plan's workspaces: the plan
-            # stays out of the pool until it has finished
+            # work still in flight may use the plan's tables and the slot's
+            # arena: both stay out of reuse until it has finished
             self.draining.append(h)
             return
+        self._idle_plan(h)
+
+    def _idle_plan(self, h):
+        if hasattr(h["plan"], "set_workspace"):
+            h["plan"].set_workspace(None)          # the arena stays with the slot
+        self.busy_slots.discard(h.get("slot"))
         self._to_idle(h["pkey"], h["plan"])
 
 

@@ -129,3 +129,35 @@ def test_chunked_host_pipeline(L):
         dev = p.fbp(d.cuda(), form="fourier", kind="shepp").cpu()
         p.fbp_host(d.pin_memory(), out, form="fourier", kind="shepp")
     assert rel(out.numpy(), dev.numpy()) < 1e-6
+
+
+def test_lent_workspace_gives_identical_results_and_allocates_nothing(L):
+    g = I.Geometry(64, 64, 32, 40, 32, 98, math.radians(20.0))    # 98 columns: the padded TMA copy too
+    d = torch.as_tensor(I.random_projections(g, 87), dtype=torch.float32).cuda()
+    with plan_for(L, g) as own, plan_for(L, g, z_chunk=8) as p:
+        ref_f = own.fbp(d, form="fourier")
+        ref_d = own.fbp(d, form="direct")
+        need = max(p.workspace_bytes("fourier"), p.workspace_bytes("direct"))
+        arena = torch.empty(need, dtype=torch.uint8, device="cuda")
+        p.set_workspace(arena)
+        out = torch.empty(p.shape_vol, dtype=torch.float32, device="cuda")
+        p.fbp(d, form="fourier", out=out)                  # loads the kernels of both forms
+        p.fbp(d, form="direct", out=out)
+        torch.cuda.synchronize()
+        free0 = torch.cuda.mem_get_info()[0]
+        for form, ref in (("fourier", ref_f), ("direct", ref_d), ("fourier", ref_f)):
+            p.fbp(d, form=form, out=out)
+            torch.cuda.synchronize()
+            assert torch.equal(out, ref), form
+        assert torch.cuda.mem_get_info()[0] == free0
+        assert p.device_bytes() < 1 << 20                  # tables only
+        # too small a buffer: a clean ENOMEM naming both sizes
+        p.set_workspace(arena[: 256 * 16])
+        with pytest.raises(L.LaminoError) as e:
+            p.fbp(d, form="fourier", out=out)
+        assert e.value.code == L.ENOMEM and "lent workspace" in str(e.value)
+        with pytest.raises(L.LaminoError) as e:
+            p.set_workspace(arena[8:])                       # not 256-byte aligned
+        assert e.value.code == L.EINVAL
+        p.set_workspace(None)                                # back to plan-owned workspaces
+        assert torch.equal(p.fbp(d, form="fourier"), ref_f)

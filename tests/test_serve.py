@@ -136,7 +136,7 @@ def test_timed_out_plan_rejoins_the_pool_only_after_its_work_finishes():
             pass
 
     b = S.CudaBackend.__new__(S.CudaBackend)
-    b.idle, b.draining, b.max_idle_plans = collections.OrderedDict(), [], 16
+    b.idle, b.draining, b.max_idle_plans, b.busy_slots = collections.OrderedDict(), [], 16, set()
     r = S.Request(0, 8, 8, 8, 4, 12, 8, 0.3, 0.0)
     pk = (r.key, 0)
     ev, plan = Ev(), object()
