@@ -91,6 +91,7 @@ struct GridArgs {
     int ch;                                  // column chunk of the statistics
     int L, l0;                               // planes of the half spectrum; first plane of
                                              // the launch (blockIdx.y = l - l0; V is [l - l0])
+    int lchunk;                              // lines per band-list chunk (>= nproj: one chunk)
     int civ_cap;                             // entries of the group table (0: none)
     float sinphi, c1, c2;  // c = -1/(4t) per axis
     float q1, q2;          // exp(2 c) per axis (gauss_taps)
@@ -227,12 +228,37 @@ __device__ __forceinline__ int block_scan(int* v, int n, int* tmp) {
 constexpr float kRoundMagic = 12582912.0f;   // 1.5 * 2^23
 constexpr int kRoundMagicBits = 0x4B400000;  // its bit pattern
 
-// The band's points, as a compact list of non-empty m-intervals over all lines:
-// every line k contributes the m in [-Wf/2 + 1, Wf/2 - 1] with Y(m) inside
-// [lo, hi) (mod M2) (band_intervals). ioff[i] = first point number of interval
-// i, ikm[i] = (k << 13) | (m start + 4096), ioff[nintv] = total. lcnt is
-// [nproj] scratch. Whole block; returns the number of points.
-__device__ __forceinline__ int band_list(const float2* __restrict__ trig, int nproj, int Wf, int M2,
+// Upper bounds on the sum and the maximum of max(|Re|, |Im|) over the band's
+// points, from the column FFT's chunk statistics of every chunk that holds a
+// point of a line's intervals (lines k = threadIdx.x + j blockDim; per-thread
+// partial results).
+__device__ __forceinline__ void band_stats(const float2* __restrict__ trig, int nproj, int Wf, int M2,
+                                           float rho, float lo, float hi, const float2* __restrict__ st,
+                                           int ch, int sstride, float& ssum, float& smax) {
+    const int half = Wf / 2;
+    for (int k = threadIdx.x; k < nproj; k += blockDim.x) {
+        int ms[4], me[4];
+        const float2 cs = __ldg(trig + k);
+        const float AY = (float)M2 * cs.y / (float)Wf, BY = -(float)M2 * rho * cs.x;
+        const int n = band_intervals(AY, BY, -half + 1, half - 1, lo, hi, M2, ms, me);
+        const float2* sl = st + (size_t)k * (Wf / ch) * sstride;
+        for (int i = 0; i < n; ++i)
+            for (int c = (ms[i] + half) / ch; c <= (me[i] + half) / ch; ++c) {
+                const float2 v = __ldg(sl + (size_t)c * sstride);
+                ssum += v.x;
+                smax = fmaxf(smax, v.y);
+            }
+    }
+}
+
+// The band's points of the lines k0 .. k0 + nk - 1, as a compact list of
+// non-empty m-intervals: every line k contributes the m in [-Wf/2 + 1,
+// Wf/2 - 1] with Y(m) inside [lo, hi) (mod M2) (band_intervals). ioff[i] =
+// first point number of interval i, ikm[i] = (k << 13) | (m start + 4096),
+// ioff[nintv] = total. lcnt is [nk] scratch; nk <= 4 blockDim. With st, also
+// the band_stats bounds of these lines. Whole block; returns the number of
+// points.
+__device__ __forceinline__ int band_list(const float2* __restrict__ trig, int k0, int nproj, int Wf, int M2,
                                          float rho, float lo, float hi, int* ioff, int* ikm,
                                          int* lcnt, int* scan_tmp, int& nintv_out,
                                          const float2* __restrict__ st = nullptr, int ch = 1,
@@ -246,12 +272,12 @@ __device__ __forceinline__ int band_list(const float2* __restrict__ trig, int np
 #pragma unroll
     for (int t = 0; t < 4; ++t) {
         nint[t] = 0;
-        const int k = threadIdx.x * per + t;
-        if (t < per && k < nproj) {
+        const int kl = threadIdx.x * per + t, k = k0 + kl;
+        if (t < per && kl < nproj) {
             const float2 cs = __ldg(trig + k);
             const float AY = (float)M2 * cs.y / (float)Wf, BY = -(float)M2 * rho * cs.x;
             nint[t] = band_intervals(AY, BY, -half + 1, half - 1, lo, hi, M2, ms[t], me[t]);
-            lcnt[k] = nint[t];
+            lcnt[kl] = nint[t];
             if (st) {
                 // every chunk that holds a point of the line's intervals: an
                 // upper bound on the band's sum and maximum
@@ -270,9 +296,9 @@ __device__ __forceinline__ int band_list(const float2* __restrict__ trig, int np
     const int nintv = block_scan(lcnt, nproj, scan_tmp);
 #pragma unroll
     for (int t = 0; t < 4; ++t) {
-        const int k = threadIdx.x * per + t;
-        if (t < per && k < nproj) {
-            const int o = lcnt[k];
+        const int kl = threadIdx.x * per + t, k = k0 + kl;
+        if (t < per && kl < nproj) {
+            const int o = lcnt[kl];
             for (int i = 0; i < nint[t]; ++i) {
                 ioff[o + i] = me[t][i] - ms[t][i] + 1;
                 ikm[o + i] = (k << 13) | (ms[t][i] + 4096);
@@ -356,10 +382,12 @@ __global__ void __launch_bounds__(1024, 1) k_grid(GridArgs a) {
     float* Uim = smf + (size_t)T2 * ld;
     // compact list of the band's non-empty m-intervals: ioff[i] = first point
     // number, ikm[i] = (line << 13) | (m start + 4096); ioff[n] = total
+    // (for one chunk of CH lines at a time when the lines do not fit at once)
+    const int CH = min(a.lchunk, nproj);
     int* ioff = reinterpret_cast<int*>(Uim + (size_t)T2 * ld);
-    int* ikm = ioff + 4 * nproj + 1;
-    int* lcnt = ikm + 4 * nproj;            // [nproj] per-line interval counts (scan)
-    int* civ = lcnt + nproj;                // [civ_cap] group table of the band list
+    int* ikm = ioff + 4 * CH + 1;
+    int* lcnt = ikm + 4 * CH;               // [CH] per-line interval counts (scan)
+    int* civ = lcnt + CH;                   // [civ_cap] group table of the band list
     __shared__ float red_s[32], red_m[32];
     __shared__ int scan_tmp[32];
     const int band = blockIdx.x, l = a.l0 + blockIdx.y;
@@ -373,15 +401,14 @@ __global__ void __launch_bounds__(1024, 1) k_grid(GridArgs a) {
     const int half = a.Wf / 2;
     // points whose 2W rows reach the band: Y in [s20 - W, s20 + T2 + W - 1);
     // the chunk statistics of the column pass bound the band's values
-    int nintv = 0;
+    int nintv = 0, total = 0;
     float lsum = 0.f, lmax = 0.f;
-    const int total = band_list(a.trig, nproj, a.Wf, M2, rho, (float)(s20 - W),
-                                (float)(s20 + T2 + W - 1), ioff, ikm, lcnt, scan_tmp, nintv,
-                                a.st + l, a.ch, a.L, &lsum, &lmax, civ, a.civ_cap);
-    const int* civ_t = (total <= 32 * a.civ_cap) ? civ : nullptr;
-    auto locate = [&](int base, int& k, int& m) -> bool {
-        return band_locate(ioff, ikm, nintv, total, base, lane, k, m, civ_t);
-    };
+    const float lo = (float)(s20 - W), hi = (float)(s20 + T2 + W - 1);
+    if (CH >= nproj)
+        total = band_list(a.trig, 0, nproj, a.Wf, M2, rho, lo, hi, ioff, ikm, lcnt, scan_tmp, nintv,
+                          a.st + l, a.ch, a.L, &lsum, &lmax, civ, a.civ_cap);
+    else   // the scale needs every line's bound before any chunk is spread
+        band_stats(a.trig, nproj, a.Wf, M2, rho, lo, hi, a.st + l, a.ch, a.L, lsum, lmax);
 
     const float2* Gl = a.G + (size_t)l * nproj * a.Wf;
 #pragma unroll
@@ -397,12 +424,19 @@ __global__ void __launch_bounds__(1024, 1) k_grid(GridArgs a) {
     S1 *= 1.01f;
     const float q = (S1 > 0.f) ? fminf(1073741824.0f / S1, 2097152.0f / Smax) : 1.0f;
 
-    // spread
+    // spread, chunk of lines by chunk of lines
     const uint32_t s_re = (uint32_t)__cvta_generic_to_shared(Ui_re);
     const uint32_t plane_bytes = 4u * (uint32_t)(T2 * ld);
+    for (int k0 = 0; k0 < nproj; k0 += CH) {
+    if (CH < nproj) {
+        __syncthreads();   // every warp is done with the previous chunk's list
+        total = band_list(a.trig, k0, min(CH, nproj - k0), a.Wf, M2, rho, lo, hi, ioff, ikm, lcnt,
+                          scan_tmp, nintv, nullptr, 1, 0, nullptr, nullptr, civ, a.civ_cap);
+    }
+    const int* civ_t = (total <= 32 * a.civ_cap) ? civ : nullptr;
     for (int base = warp * 32; base < total; base += nwarps * 32) {
         int k, m;
-        if (!locate(base, k, m)) continue;
+        if (!band_locate(ioff, ikm, nintv, total, base, lane, k, m, civ_t)) continue;
         float2 g = Gl[(size_t)k * a.Wf + (m + half)];
         g.x *= q;
         g.y *= q;
@@ -449,6 +483,7 @@ __global__ void __launch_bounds__(1024, 1) k_grid(GridArgs a) {
             }
         }
     }
+    }   // chunks of lines
     __syncthreads();
     // back to float
     const float inv_q = 1.0f / q;
@@ -649,9 +684,10 @@ __global__ void __launch_bounds__(512, 1) k_grid_t(GridArgs a, const float2* __r
     const int M1 = a.M1, M2 = a.M2, T2 = a.T2, ld = a.ld, NR = T2 + 2 * W - 1;
     const int nproj = a.nproj, n0 = a.n0;
     float2* X = smx;                                           // [NR][ld]
+    const int CH = min(a.lchunk, nproj);                       // lines per band-list chunk
     int* ioff = reinterpret_cast<int*>(X + (size_t)NR * ld);
-    int* ikm = ioff + 4 * nproj + 1;
-    int* lcnt = ikm + 4 * nproj;
+    int* ikm = ioff + 4 * CH + 1;
+    int* lcnt = ikm + 4 * CH;
     __shared__ int scan_tmp[32];
     const int band = blockIdx.x, l = a.l0 + blockIdx.y, s20 = band * T2;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
@@ -671,12 +707,14 @@ __global__ void __launch_bounds__(512, 1) k_grid_t(GridArgs a, const float2* __r
 
     const float rho = (float)l * a.sinphi / (float)a.Hf;
     // owners: first tap row fy - W + 1 in [s20, s20 + T2), i.e. Y in [s20 + W - 1, s20 + T2 + W - 1)
-    int nintv = 0;
-    const int total = band_list(a.trig, nproj, a.Wf, M2, rho, (float)(s20 + W - 1),
-                                (float)(s20 + T2 + W - 1), ioff, ikm, lcnt, scan_tmp, nintv);
     float2* Gl = Gt + (size_t)l * nproj * a.Wf;
     if (band == 0)   // the dropped Nyquist column m = -Wf/2
         for (int k = threadIdx.x; k < nproj; k += blockDim.x) Gl[(size_t)k * a.Wf] = make_float2(0.f, 0.f);
+    for (int k0 = 0; k0 < nproj; k0 += CH) {
+    if (k0 > 0) __syncthreads();   // every warp is done with the previous chunk's list
+    int nintv = 0;
+    const int total = band_list(a.trig, k0, min(CH, nproj - k0), a.Wf, M2, rho, (float)(s20 + W - 1),
+                                (float)(s20 + T2 + W - 1), ioff, ikm, lcnt, scan_tmp, nintv);
     for (int base = warp * 32; base < total; base += nwarps * 32) {
         int k, m;
         if (!band_locate(ioff, ikm, nintv, total, base, lane, k, m)) continue;
@@ -721,6 +759,7 @@ __global__ void __launch_bounds__(512, 1) k_grid_t(GridArgs a, const float2* __r
         }
         Gl[(size_t)k * a.Wf + (m + half)] = acc;
     }
+    }   // chunks of lines
 }
 
 // Column pass transpose: plane values of one (projection, column) x conj(phase)
@@ -876,6 +915,18 @@ int launch_colfft(lamino_plan_t p, const FourierBufs& fb, int k0, int k1, cudaSt
     return LAMINO_OK;
 }
 
+// Lines per band-list chunk of the gridding kernels: all nproj lines if their
+// lists (9 ints per line) fit in shared memory beside a band of band_bytes,
+// else the most that do (at least 512 and at most 4 per thread, maxlines), with
+// 4 KB kept for the group table; 0 if not even 512 fit.
+static int line_chunk(int nproj, size_t band_bytes, int maxlines) {
+    const size_t avail = 220 * 1024 - 4096;
+    if (band_bytes + sizeof(int) * 10 >= avail) return 0;
+    const long fit = (long)((avail - band_bytes - sizeof(int)) / (9 * sizeof(int)));
+    const long ch = std::min<long>(std::min<long>(fit, maxlines), nproj);
+    return ch >= std::min(nproj, 512) ? (int)ch : 0;
+}
+
 // Arguments of the gridding kernel and of its transpose shared by both.
 static GridArgs grid_args(lamino_plan_t p) {
     GridArgs a;
@@ -883,7 +934,7 @@ static GridArgs grid_args(lamino_plan_t p) {
     a.trig = p->d_trig; a.dec1 = p->d_dec1;
     a.ch = 1; a.civ_cap = 0;
     a.nproj = p->nproj; a.Wf = p->Wf; a.Hf = p->Hf; a.n0 = p->n0; a.M1 = p->M1; a.M2 = p->M2;
-    a.L = p->L; a.l0 = 0;
+    a.L = p->L; a.l0 = 0; a.lchunk = p->nproj;
     a.sinphi = (float)sin(p->tilt);
     a.c1 = (float)(-1.0 / (4.0 * p->t1));
     a.c2 = (float)(-1.0 / (4.0 * p->t2));
@@ -908,12 +959,14 @@ int launch_grid(lamino_plan_t p, const FourierBufs& fb, int l0, int l1, cudaStre
     while (T2 > 1 && (size_t)T2 * a.ld * sizeof(float2) > 132 * 1024) T2 /= 2;
     while (p->M2 % T2) T2 /= 2;
     a.T2 = T2;
-    // band accumulator (planar) + compact interval list + per-line counts
-    if (p->nproj > 4 * 768 || p->Wf > 8192)
-        return fail(p, LAMINO_EUNSUPPORTED, "gridding supports up to 3072 angles and Wf <= 8192");
-    size_t smem = (size_t)T2 * a.ld * sizeof(float2) + sizeof(int) * (9 * (size_t)p->nproj + 1);
-    if (smem > 220 * 1024)
-        return fail(p, LAMINO_EUNSUPPORTED, "gridding tile of %zu bytes exceeds shared memory", smem);
+    // band accumulator (planar) + compact interval list + per-line counts, for
+    // chunks of lines when every line's list does not fit beside the band
+    if (p->Wf > 8192) return fail(p, LAMINO_EUNSUPPORTED, "gridding supports Wf <= 8192");
+    const size_t band_bytes = (size_t)T2 * a.ld * sizeof(float2);
+    a.lchunk = line_chunk(p->nproj, band_bytes, 4 * 1024);
+    if (a.lchunk <= 0)
+        return fail(p, LAMINO_EUNSUPPORTED, "gridding tile of %zu bytes exceeds shared memory", band_bytes);
+    size_t smem = band_bytes + sizeof(int) * (9 * (size_t)std::min(a.lchunk, p->nproj) + 1);
     // group table in what is left (bands with more points bisect instead)
     a.civ_cap = (int)std::min<size_t>(16384, (224 * 1024 - smem) / sizeof(int));
     smem += sizeof(int) * (size_t)a.civ_cap;
@@ -1012,8 +1065,7 @@ int launch_project_fourier(lamino_plan_t p, const FourierBufs& fb, const float* 
     float2* Vt = fb.V;   // [zc][n0][M2]
     float2* Gt = fb.G;   // [L][nproj][Wf]
     float2* Rt = fb.R;   // [nproj][H][Wf]
-    if (p->nproj > 4 * 512 || p->Wf > 8192)
-        return fail(p, LAMINO_EUNSUPPORTED, "Fourier projector supports up to 2048 angles");
+    if (p->Wf > 8192) return fail(p, LAMINO_EUNSUPPORTED, "Fourier projector supports Wf <= 8192");
     {   // x3
         const FftDesc& f = p->fM3;
         int C = 16;
@@ -1037,9 +1089,11 @@ int launch_project_fourier(lamino_plan_t p, const FourierBufs& fb, const float* 
     while (T2 > 1 && (size_t)(T2 + 2 * p->w - 1) * a.ld * sizeof(float2) > 150 * 1024) T2 /= 2;
     while (p->M2 % T2) T2 /= 2;
     a.T2 = T2;
-    const size_t gsmem = (size_t)(T2 + 2 * p->w - 1) * a.ld * sizeof(float2) + sizeof(int) * (9 * (size_t)p->nproj + 1);
-    if (gsmem > 220 * 1024)
-        return fail(p, LAMINO_EUNSUPPORTED, "gridding transpose tile of %zu bytes exceeds shared memory", gsmem);
+    const size_t tile = (size_t)(T2 + 2 * p->w - 1) * a.ld * sizeof(float2);
+    a.lchunk = line_chunk(p->nproj, tile, 4 * 512);
+    if (a.lchunk <= 0)
+        return fail(p, LAMINO_EUNSUPPORTED, "gridding transpose tile of %zu bytes exceeds shared memory", tile);
+    const size_t gsmem = tile + sizeof(int) * (9 * (size_t)std::min(a.lchunk, p->nproj) + 1);
     for (int l0 = 0; l0 < p->L; l0 += fb.zc) {
         const int l1 = std::min(p->L, l0 + fb.zc);
         {   // x2 of planes [l0, l1): Pt -> Vt (chunk-relative)
