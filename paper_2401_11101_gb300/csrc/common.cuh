@@ -15,11 +15,14 @@
 namespace lam {
 
 // Largest FFT length any kernel handles (one sequence fits in shared memory),
-// and the most threads one sequence may take (n / elements per thread): the
-// FFT kernels run blocks of at most 512 threads, and a block must hold at
-// least one whole sequence. So 2^k lengths go up to 4096, 3*2^k up to 6144.
+// and the most threads one sequence may take (n / elements per thread): a
+// block must hold at least one whole sequence. So 2^k lengths go up to 8192,
+// 3*2^k up to 6144. Most FFT kernels run blocks of at most 512 threads
+// (lengths up to 4096); the filter, the row pass, the gridding and the x2 pass
+// also have 1024-thread instantiations for 8192-point sequences, and the
+// others refuse such lengths (EUNSUPPORTED).
 constexpr int kMaxFft = 8192;
-constexpr int kMaxFftThreads = 512;
+constexpr int kMaxFftThreads = 1024;
 
 // Radix schedule of one FFT length: n = product of the stage radices, stage
 // st having radix (rads >> 4 st) & 15; power-of-two radices come first and a

@@ -39,8 +39,8 @@ __device__ __forceinline__ void load_pair_rows(const Tin* __restrict__ d, float2
 
 // Filter: rows of length W zero-padded to Wp, FFT, x H(f)/Wp, IFFT, crop.
 // One CTA handles `pairs` row pairs; each pair uses t = Wp/E threads.
-template <int E, typename Tin>
-__global__ void __launch_bounds__(512, 1) k_filter(const Tin* __restrict__ d, float* __restrict__ q,
+template <int E, typename Tin, int MT>
+__global__ void __launch_bounds__(MT, 1) k_filter(const Tin* __restrict__ d, float* __restrict__ q,
                                                 long row0, long row1, int W, FftDesc fp,
                                                 const float* __restrict__ filt, int pairs) {
     extern __shared__ float2 sm[];
@@ -75,8 +75,8 @@ __global__ void __launch_bounds__(512, 1) k_filter(const Tin* __restrict__ d, fl
 // two real spectra and writes them in signed frequency order mi = m + Wf/2,
 // multiplied by the centring phase exp(2 pi i m cu/Wf) (zero at m = -Wf/2).
 // Output R[row][mi], row = k*H + r.
-template <int EP, int EF, typename Tin>
-__global__ void __launch_bounds__(512, 1) k_rowfft(const Tin* __restrict__ d, float2* __restrict__ R,
+template <int EP, int EF, typename Tin, int MT>
+__global__ void __launch_bounds__(MT, 1) k_rowfft(const Tin* __restrict__ d, float2* __restrict__ R,
                                                 long row0, long row1, int W, int offu, FftDesc fp,
                                                 FftDesc ff, const float* __restrict__ filt,
                                                 const float2* __restrict__ phu, int pairs, int T) {
@@ -329,13 +329,13 @@ int filter_typed(lamino_plan_t p, const Tin* d, float* q, int kind, cudaStream_t
     dim3 grid((unsigned)((npairs + pairs - 1) / pairs));
     const float* filt = p->d_filt + (size_t)kind * p->Wp;
     ProfScope prof(p, "filter", s);
-    if (f.e == 8) {
-        cudaFuncSetAttribute(k_filter<8, Tin>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-        k_filter<8, Tin><<<grid, pairs * f.t, smem, s>>>(d, q, row0, row1, p->W, f, filt, pairs);
-    } else {
-        cudaFuncSetAttribute(k_filter<12, Tin>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-        k_filter<12, Tin><<<grid, pairs * f.t, smem, s>>>(d, q, row0, row1, p->W, f, filt, pairs);
-    }
+    auto go = [&](auto kern) {
+        cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        kern<<<grid, pairs * f.t, smem, s>>>(d, q, row0, row1, p->W, f, filt, pairs);
+    };
+    if (pairs * f.t > 512) go(k_filter<8, Tin, 1024>);      // 8192-point rows
+    else if (f.e == 8) go(k_filter<8, Tin, 512>);
+    else go(k_filter<12, Tin, 512>);
     LAM_LAUNCH_CHECK(p, "filter kernel");
     return LAMINO_OK;
 }
@@ -351,7 +351,14 @@ int rowfft_launch(lamino_plan_t p, const Tin* d, float2* R, const float* filt, c
     if (npairs <= 0) return LAMINO_OK;
     size_t smem = per_pair * pairs;
     dim3 grid((unsigned)((npairs + pairs - 1) / pairs));
-    auto kern = k_rowfft<EP, EF, Tin>;
+    // 1024 threads per row pair only for 8192-point rows (filter length 2^13:
+    // EP = 8, or an unfiltered 2^13 Fourier row: EP = 0, EF = 8)
+    auto kern = k_rowfft<EP, EF, Tin, 512>;
+    if constexpr (EP == 8 || (EP == 0 && EF == 8)) {
+        if (pairs * T > 512) kern = k_rowfft<EP, EF, Tin, 1024>;
+    } else {
+        if (pairs * T > 512) return fail(p, LAMINO_EUNSUPPORTED, "row FFT block of %d threads", pairs * T);
+    }
     cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     ProfScope prof(p, EP > 0 ? "filter_rowfft" : "rowfft", s);
     kern<<<grid, pairs * T, smem, s>>>(d, R, row0, row1, p->W, p->offu, p->fWp, p->fWf, filt,

@@ -506,8 +506,8 @@ __global__ void __launch_bounds__(1024, 1) k_grid(GridArgs a) {
 }
 
 // ---------------------------------------------------------------- colifft
-template <int E>
-__global__ void __launch_bounds__(512, 2) k_colifft(const float2* __restrict__ V, float2* __restrict__ P,
+template <int E, int MT>
+__global__ void __launch_bounds__(MT, MT > 512 ? 1 : 2) k_colifft(const float2* __restrict__ V, float2* __restrict__ P,
                                                   int n0, int n1, FftDesc f2,
                                                   const float* __restrict__ dec2, int C, int l0) {
     extern __shared__ float2 sm[];
@@ -602,7 +602,13 @@ void set_smem(K kern, size_t smem) {
 // paths), else f.t per sequence; 128 to 512.
 int fft_block_threads(const FftDesc& f, int C) {
     const int per = (f.e == 8 && f.n == 512) ? 32 : (f.e == 8 && f.n == 1024) ? 64 : f.t;
-    return std::min(512, std::max(128, C * per));
+    return std::min(f.t > 512 ? 1024 : 512, std::max(128, C * per));
+}
+
+// Kernels whose blocks hold at most 512 threads refuse sequences that need more.
+int refuse_long_fft(lamino_plan_t p, const FftDesc& f, const char* what) {
+    return fail(p, LAMINO_EUNSUPPORTED, "%s supports FFT lengths up to 4096 (2^k) or 6144 (3*2^k), "
+                "not %d", what, f.n);
 }
 
 
@@ -897,6 +903,7 @@ int launch_colfft(lamino_plan_t p, const FourierBufs& fb, int k0, int k1, cudaSt
     if (k1 <= k0) return LAMINO_OK;
     // column FFT (+ chunk statistics for the gridding bound, after G in B)
     const FftDesc& f = p->fHf;
+    if (f.t > 512) return refuse_long_fft(p, f, "the column FFT (padded detector height)");
     const int C = fb.CH;
     size_t smem = (size_t)C * (f.n + 1) * sizeof(float2);
     dim3 grid(p->Wf / C, k1 - k0);
@@ -996,13 +1003,13 @@ int launch_colifft(lamino_plan_t p, const FourierBufs& fb, int l0, int l1, cudaS
     dim3 grid((p->n0 + C - 1) / C, l1 - l0);
     int threads = fft_block_threads(f, C);
     ProfScope prof(p, "colifft", s);
-    if (f.e == 8) {
-        set_smem(k_colifft<8>, smem);
-        k_colifft<8><<<grid, threads, smem, s>>>(fb.V, fb.P, p->n0, p->n1, f, p->d_dec2, C, l0);
-    } else {
-        set_smem(k_colifft<12>, smem);
-        k_colifft<12><<<grid, threads, smem, s>>>(fb.V, fb.P, p->n0, p->n1, f, p->d_dec2, C, l0);
-    }
+    auto go = [&](auto kern) {
+        set_smem(kern, smem);
+        kern<<<grid, threads, smem, s>>>(fb.V, fb.P, p->n0, p->n1, f, p->d_dec2, C, l0);
+    };
+    if (threads > 512) go(k_colifft<8, 1024>);          // 8192-point x2 grids
+    else if (f.e == 8) go(k_colifft<8, 512>);
+    else go(k_colifft<12, 512>);
     LAM_LAUNCH_CHECK(p, "x2 inverse FFT kernel");
     return LAMINO_OK;
 }
@@ -1011,6 +1018,7 @@ int launch_zusfft(lamino_plan_t p, const FourierBufs& fb, float* vol, int i10, i
     if (i11 <= i10) return LAMINO_OK;
     // x3 USFFT of the columns of x2 rows [i10, i11)
     const FftDesc& f = p->fM3;
+    if (f.t > 512) return refuse_long_fft(p, f, "the x3 USFFT");
     int C = 16;
     auto bytes = [&](int c) { return (size_t)c * ((size_t)p->L + f.n + 1) * sizeof(float2); };
     while (C > 1 && bytes(C) > 72 * 1024) C /= 2;
@@ -1065,7 +1073,8 @@ int launch_project_fourier(lamino_plan_t p, const FourierBufs& fb, const float* 
     float2* Vt = fb.V;   // [zc][n0][M2]
     float2* Gt = fb.G;   // [L][nproj][Wf]
     float2* Rt = fb.R;   // [nproj][H][Wf]
-    if (p->Wf > 8192) return fail(p, LAMINO_EUNSUPPORTED, "Fourier projector supports Wf <= 8192");
+    for (const FftDesc* f : {&p->fM3, &p->fM2, &p->fM1, &p->fHf, &p->fWf})
+        if (f->t > 512) return refuse_long_fft(p, *f, "the Fourier projector");
     {   // x3
         const FftDesc& f = p->fM3;
         int C = 16;

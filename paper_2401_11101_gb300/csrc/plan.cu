@@ -549,7 +549,7 @@ int lamino_plan(lamino_plan_t* out, int n0, int n1, int n2, int nproj, int det_w
         char buf[256];
         for (int n : lens)
             if (!fft_len_ok(n) && p->fourier_ok) {
-                snprintf(buf, sizeof buf, "FFT length %d of the Fourier form is not 2^k (8 .. 4096) "
+                snprintf(buf, sizeof buf, "FFT length %d of the Fourier form is not 2^k (8 .. 8192) "
                          "or 3*2^k (12 .. 6144)", n);
                 p->fourier_why = buf;
                 p->fourier_ok = false;

@@ -450,9 +450,9 @@ def test_many_angles_in_chunks_of_lines(L):
 
 
 def test_unsupported_sizes_fail_cleanly(L):
-    # a 4096-wide volume needs 8192-point x1/x2 grids: more threads per FFT
-    # than a block of the FFT kernels holds, so the plan refuses the Fourier form
-    g = I.Geometry(4096, 4096, 2, 2, 2, 64, math.radians(20.0))
+    # an 8192-wide volume needs 16384-point x1/x2 grids: longer than any FFT
+    # of the library, so the plan refuses the Fourier form
+    g = I.Geometry(8192, 8192, 2, 2, 2, 64, math.radians(20.0))
     q = torch.as_tensor(I.random_projections(g, 30), dtype=torch.float32).cuda()
     with plan_for(L, g) as p:
         with pytest.raises(L.LaminoError) as e:
