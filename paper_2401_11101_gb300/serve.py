@@ -120,6 +120,10 @@ class Report:
             "queue_wait_p50_ms": float(np.percentile([(o.admitted - o.arrival) * 1e3 for o in self.outcomes
                                                       if o.status == "ok"], 50)) if len(lat) else None,
             "gvox_s": vox / self.wall_s / 1e9 if self.wall_s > 0 else None,
+            # the stream's own rate: all requests' voxels over the arrival span
+            # (a server that keeps up delivers about this much)
+            "offered_gvox_s": (sum(r.nvox for r in requests) / max(o.arrival for o in self.outcomes) / 1e9
+                               if self.outcomes and max(o.arrival for o in self.outcomes) > 0 else None),
             "wall_s": self.wall_s,
             "busy_s": self.busy_s,
             "queued_max": max((s[1] for s in tl), default=0),
