@@ -81,7 +81,7 @@ typedef struct {
                         slices, the 1D USFFT by chunks of columns, the direct form by
                         chunks of x3 slices): k_v planes per chunk of the gridding and
                         the x2 pass, and output slices per launch of the direct form
-                        (rounded up to its 16-slice tile); 0: no chunking. Chunking the
+                        (rounded up to its 32-slice tile); 0: no chunking. Chunking the
                         Fourier form keeps only one chunk of x1-pass planes and shrinks
                         its workspace (lamino_workspace_bytes); results are equal */
 } lamino_opts;

@@ -29,7 +29,7 @@ namespace {
 // Backprojector tile: BX x BY columns x BZ slices; each of the 256 consumer
 // threads owns two columns (x2 = y and y + BY/2) whose updates run as packed
 // f32x2 arithmetic. Projector tile (k_project): TX x TY columns x TZ slices.
-constexpr int BX = 32, BY = 16, BZ = 16;
+constexpr int BX = 32, BY = 16, BZ = 32;
 constexpr int TX = 32, TY = 8, TZ = 32;
 constexpr int kConsumers = 256;                  // 8 warps
 constexpr int kThreads = kConsumers + 32;        // + 1 producer warp

@@ -957,11 +957,13 @@ int launch_grid(lamino_plan_t p, const FourierBufs& fb, int l0, int l1, cudaStre
     GridArgs a = grid_args(p);
     a.G = fb.G; a.V = fb.V; a.st = fb.st; a.ch = fb.CH;
     a.l0 = l0;
-    // Row pitch = 5 (mod 32) words: lanes holding consecutive points of one
-    // line (steps of ~1.33 cells) then fall in different banks for all but
-    // a narrow wedge of line directions (a pitch of 1 mod 32 stacks every
-    // near-anti-diagonal line into one bank).
-    a.ld = p->M1 + ((5 - p->M1) % 32 + 32) % 32;
+    // Row pitch = 13 (mod 32) words. Lanes hold consecutive points of one
+    // line (steps of ~1.33 cells), so a warp's reductions span ~42 cells along
+    // the line and some banks take two lanes whatever the pitch; simulating the
+    // reductions of the 512x512x256 workload's bands over all residues gives
+    // 2.11 wavefronts per reduction at 13 (and 19), 2.25 at 5, 2.66 at 1 (which
+    // stacks near-anti-diagonal lines into one bank), 3.35 at 0.
+    a.ld = p->M1 + ((13 - p->M1) % 32 + 32) % 32;
     int T2 = p->grid_rows > 0 ? p->grid_rows : 16;
     while (T2 > 1 && (size_t)T2 * a.ld * sizeof(float2) > 132 * 1024) T2 /= 2;
     while (p->M2 % T2) T2 /= 2;

@@ -396,7 +396,8 @@ void box_for(DirectCfg& c, double tilt) {
 }
 
 void direct_config(lamino_plan_t p) {
-    p->dcfg = DirectCfg();                      // 32 x 16 x 16
+    p->dcfg = DirectCfg();                      // 32 x 16 x 32
+    p->dcfg.tz = 32;
     box_for(p->dcfg, p->tilt);
     p->pcfg = DirectCfg();
     p->pcfg.ty = 8;
