@@ -470,19 +470,20 @@ __device__ __forceinline__ void twiddle8(float2* v, const float2* __restrict__ t
 // twiddles w32^(re); a radix-4 DFT over r between the lanes of a quad (two
 // shuffle butterflies, as in fft1024_pair) gives X[c + 8e + 64q], lane r
 // producing q = 2 (r % 2) + r / 2. tw: exp(-2 pi i u / 256), u in [0, 256).
-__device__ __forceinline__ void fft256_warp(float2* x, const float2* __restrict__ tw, float s, int lane) {
+template <typename S>
+__device__ __forceinline__ void fft256_warp_s(S x, const float2* __restrict__ tw, float s, int lane) {
     float2 v[8];
 #pragma unroll
-    for (int a = 0; a < 8; ++a) v[a] = x[32 * a + lane];
+    for (int a = 0; a < 8; ++a) v[a] = x.ld(32 * a + lane);
     bfly<8>(v, s);
     twiddle8(v, tw, lane, s);
     __syncwarp();
 #pragma unroll
-    for (int c = 0; c < 8; ++c) x[32 * c + ((lane + 4 * c) & 31)] = v[c];
+    for (int c = 0; c < 8; ++c) x.st(32 * c + ((lane + 4 * c) & 31), v[c]);
     __syncwarp();
     const int c = lane >> 2, r = lane & 3;
 #pragma unroll
-    for (int m = 0; m < 8; ++m) v[m] = x[32 * c + ((4 * m + r + 4 * c) & 31)];
+    for (int m = 0; m < 8; ++m) v[m] = x.ld(32 * c + ((4 * m + r + 4 * c) & 31));
     bfly<8>(v, s);
     twiddle8(v, tw, 8 * r, s);
     const int b1 = r >> 1, b0 = r & 1;
@@ -502,8 +503,12 @@ __device__ __forceinline__ void fft256_warp(float2* x, const float2* __restrict_
         float2 o;
         o.x = __shfl_xor_sync(0xffffffffu, v[e].x, 1);
         o.y = __shfl_xor_sync(0xffffffffu, v[e].y, 1);
-        x[c + 8 * e + 64 * q] = b0 ? csub(o, v[e]) : cadd(v[e], o);
+        x.st(c + 8 * e + 64 * q, b0 ? csub(o, v[e]) : cadd(v[e], o));
     }
+}
+
+__device__ __forceinline__ void fft256_warp(float2* x, const float2* __restrict__ tw, float s, int lane) {
+    fft256_warp_s(SeqC{x}, tw, s, lane);
 }
 
 // 512-point FFT of the sequence x (shared memory, natural order in and out,
@@ -518,19 +523,20 @@ __device__ __forceinline__ void fft256_warp(float2* x, const float2* __restrict_
 // instead of one per radix-8 stage, and only warp barriers. The transpose
 // rotates row c by 2c slots so that its row writes and its column reads both
 // take the minimum two wavefronts. tw: exp(-2 pi i u / 512), u in [0, 512).
-__device__ __forceinline__ void fft512_warp(float2* x, const float2* __restrict__ tw, float s, int lane) {
+template <typename S>
+__device__ __forceinline__ void fft512_warp_s(S x, const float2* __restrict__ tw, float s, int lane) {
     float2 v[16];
 #pragma unroll
-    for (int a = 0; a < 16; ++a) v[a] = x[32 * a + lane];
+    for (int a = 0; a < 16; ++a) v[a] = x.ld(32 * a + lane);
     dft16(v, s);
     twiddle16(v, tw, lane, s);
     __syncwarp();
 #pragma unroll
-    for (int c = 0; c < 16; ++c) x[32 * c + ((lane + 2 * c) & 31)] = v[c];
+    for (int c = 0; c < 16; ++c) x.st(32 * c + ((lane + 2 * c) & 31), v[c]);
     __syncwarp();
     const int c = lane >> 1, p = lane & 1;
 #pragma unroll
-    for (int m = 0; m < 16; ++m) v[m] = x[32 * c + ((2 * m + p + 2 * c) & 31)];
+    for (int m = 0; m < 16; ++m) v[m] = x.ld(32 * c + ((2 * m + p + 2 * c) & 31));
     dft16(v, s);
     // odd lanes: w32^e, cos and sin of pi e / 16
     const float a1 = 0.98078528040323044913f, a3 = 0.83146961230254523708f;
@@ -560,8 +566,12 @@ __device__ __forceinline__ void fft512_warp(float2* x, const float2* __restrict_
         float2 o;
         o.x = __shfl_xor_sync(0xffffffffu, v[e].x, 1);
         o.y = __shfl_xor_sync(0xffffffffu, v[e].y, 1);
-        x[c + 16 * e + 256 * p] = p ? csub(o, v[e]) : cadd(v[e], o);
+        x.st(c + 16 * e + 256 * p, p ? csub(o, v[e]) : cadd(v[e], o));
     }
+}
+
+__device__ __forceinline__ void fft512_warp(float2* x, const float2* __restrict__ tw, float s, int lane) {
+    fft512_warp_s(SeqC{x}, tw, s, lane);
 }
 
 // 1024-point FFT of the sequence x (as fft512_warp) by the 64 threads of one
@@ -574,20 +584,31 @@ __device__ __forceinline__ void fft512_warp(float2* x, const float2* __restrict_
 // its twiddles w64^(re); the radix-4 DFT over r between the four lanes of a
 // quad (two shuffle butterflies) gives X[c + 16e + 256q] = sum_r w4^(rq)
 // w64^(re) D_r[e], lane r producing q = 2 (r % 2) + r / 2.
-__device__ __forceinline__ void fft1024_pair(float2* x, const float2* __restrict__ tw, float s, int tid,
-                                             int bar) {
+// The sequence is any storage view (SeqC, SeqP); the pair synchronises with
+// fft_sync(smode, gid, 64), i.e. named barrier 1 + gid, or the whole block
+// (smode 0) when every pair of the block runs one sequence in step. A pair
+// with active == false touches no memory and only takes part in the barriers.
+// With swz, output k is stored at k ^ (((k >> 8) & 3) << 3) (fft1024_pos):
+// the last stores of a warp then fill all 32 banks of 4-byte words instead of
+// 8 (four quads' q outputs share their low five bits), which pays for planar
+// sequences.
+template <typename S>
+__device__ __forceinline__ void fft1024_pair_s(S x, const float2* __restrict__ tw, float s, int tid,
+                                               int smode, int gid, bool active = true, bool swz = false) {
     float2 v[16];
 #pragma unroll
-    for (int a = 0; a < 16; ++a) v[a] = x[64 * a + tid];
+    for (int a = 0; a < 16; ++a) v[a] = active ? x.ld(64 * a + tid) : make_float2(0.f, 0.f);
     dft16(v, s);
     twiddle16(v, tw, tid, s);
-    fft_sync(2, bar - 1, 64);
+    fft_sync(smode, gid, 64);
 #pragma unroll
-    for (int c = 0; c < 16; ++c) x[64 * c + ((tid + 4 * c) & 63)] = v[c];
-    fft_sync(2, bar - 1, 64);
+    for (int c = 0; c < 16; ++c)
+        if (active) x.st(64 * c + ((tid + 4 * c) & 63), v[c]);
+    fft_sync(smode, gid, 64);
     const int c = tid >> 2, r = tid & 3;
 #pragma unroll
-    for (int m = 0; m < 16; ++m) v[m] = x[64 * c + ((4 * m + r + 4 * c) & 63)];
+    for (int m = 0; m < 16; ++m)
+        v[m] = active ? x.ld(64 * c + ((4 * m + r + 4 * c) & 63)) : make_float2(0.f, 0.f);
     dft16(v, s);
     twiddle16(v, tw, 16 * r, s);
     const int b1 = r >> 1, b0 = r & 1;
@@ -601,15 +622,21 @@ __device__ __forceinline__ void fft1024_pair(float2* x, const float2* __restrict
         if (b1 & b0) a = cmul_si(a, s);
         v[e] = a;
     }
-    fft_sync(2, bar - 1, 64);   // every read of x precedes the writes below
+    fft_sync(smode, gid, 64);   // every read of x precedes the writes below
     const int q = 2 * b0 + b1;
+    const int xo = swz ? (q << 3) : 0;
 #pragma unroll
     for (int e = 0; e < 16; ++e) {
         float2 o;
         o.x = __shfl_xor_sync(0xffffffffu, v[e].x, 1);
         o.y = __shfl_xor_sync(0xffffffffu, v[e].y, 1);
-        x[c + 16 * e + 256 * q] = b0 ? csub(o, v[e]) : cadd(v[e], o);
+        if (active) x.st((c + 16 * e + 256 * q) ^ xo, b0 ? csub(o, v[e]) : cadd(v[e], o));
     }
+}
+
+__device__ __forceinline__ void fft1024_pair(float2* x, const float2* __restrict__ tw, float s, int tid,
+                                             int bar) {
+    fft1024_pair_s(SeqC{x}, tw, s, tid, 2, bar - 1);
 }
 
 // FFTs of nseq sequences at base + i*ld with every thread of the block: groups
@@ -649,11 +676,47 @@ __device__ __forceinline__ void fft_many(float2* base, int ld, int nseq, const F
     if (mode != 0) __syncthreads();
 }
 
-// The same for planar sequences re + i*ld, im + i*ld.
-// Ends with a block-wide barrier.
+// Whether fft_many_planar<E> takes the pair path for f (see below).
+template <int E>
+__device__ __forceinline__ bool fft_planar_pair(const FftDesc& f) {
+    return E == 8 && f.n == 1024 && (blockDim.x & 63) == 0;
+}
+// Where output i of fft_many_planar<E>(..., swz) sits in its sequence.
+template <int E>
+__device__ __forceinline__ int fft_planar_pos(const FftDesc& f, int i, bool swz) {
+    return (swz && fft_planar_pair<E>(f)) ? i ^ (((i >> 8) & 3) << 3) : i;
+}
+
+// The same for planar sequences re + i*ld, im + i*ld: lengths 256 and 512
+// one sequence per warp, 1024 one per pair of warps (named barriers for at
+// most 15 pairs, else block barriers with every pair in step, idle pairs
+// taking part in the barriers only; outputs permuted as fft_planar_pos says
+// when swz). Ends with a block-wide barrier.
 template <int E>
 __device__ __forceinline__ void fft_many_planar(float* re, float* im, int ld, int nseq,
-                                                const FftDesc& f, float s) {
+                                                const FftDesc& f, float s, bool swz = false) {
+    if constexpr (E == 8) {
+        if ((f.n == 256 || f.n == 512) && (blockDim.x & 31) == 0) {
+            const int lane = threadIdx.x & 31;
+            for (int seq = threadIdx.x >> 5; seq < nseq; seq += blockDim.x >> 5) {
+                const size_t o = (size_t)seq * ld;
+                if (f.n == 256) fft256_warp_s(SeqP{re + o, im + o}, f.tw, s, lane);
+                else fft512_warp_s(SeqP{re + o, im + o}, f.tw, s, lane);
+            }
+            __syncthreads();
+            return;
+        }
+        if (fft_planar_pair<E>(f)) {
+            const int np = blockDim.x >> 6, g = threadIdx.x >> 6, tid = threadIdx.x & 63;
+            const int mode = (np <= 15) ? 2 : 0;
+            for (int s0 = 0; s0 < nseq; s0 += np) {
+                const size_t o = (size_t)min(s0 + g, nseq - 1) * ld;
+                fft1024_pair_s(SeqP{re + o, im + o}, f.tw, s, tid, mode, g, s0 + g < nseq, swz);
+            }
+            __syncthreads();
+            return;
+        }
+    }
     const int T = f.t;
     const int par = blockDim.x / T;
     if (par == 0) return;   // a sequence needs more threads than the block has (the plan refuses this)

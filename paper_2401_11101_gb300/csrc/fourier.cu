@@ -493,13 +493,14 @@ __global__ void __launch_bounds__(1024, 1) k_grid(GridArgs a) {
     }
     __syncthreads();
     // inverse FFT of each band row along x1 (sum_s U(s) exp(+2 pi i x s/M1))
-    fft_many_planar<E>(Ure, Uim, ld, T2, a.f1, +1.f);
+    fft_many_planar<E>(Ure, Uim, ld, T2, a.f1, +1.f, true);
     // crop x1 in [-n0/2, n0/2), deconvolve, write V[l][i0][s2] (s2 fastest)
     const int n0 = a.n0;
     for (int idx = threadIdx.x; idx < T2 * n0; idx += blockDim.x) {
         int rr = idx % T2, i0 = idx / T2;
         int s1 = i0 - n0 / 2;
         s1 += (s1 < 0) ? M1 : 0;
+        s1 = fft_planar_pos<E>(a.f1, s1, true);
         const float dd = __ldg(a.dec1 + i0);
         a.V[((size_t)blockIdx.y * n0 + i0) * M2 + s20 + rr] = make_float2(Ure[rr * ld + s1] * dd, Uim[rr * ld + s1] * dd);
     }
