@@ -178,9 +178,11 @@ def kernel_algorithmic(p_info, g, esz_in=4):
     Wf, L = p_info["wf"], p_info["planes"]
     M2, n0, n1, n2 = p_info["m2"], g.n0, g.n1, g.n2
     c = 8  # complex64
+    # row spectra R hold the frequencies m in [0, Wf/2) (real rows: -m is the
+    # conjugate); the column pass writes both signs of m (all but the Nyquist)
     return {
-        "filter_rowfft": ("hbm", nproj * H * W * esz_in + nproj * H * Wf * c),
-        "colfft": ("hbm", nproj * H * Wf * c + L * nproj * Wf * c),
+        "filter_rowfft": ("hbm", nproj * H * W * esz_in + nproj * H * (Wf // 2) * c),
+        "colfft": ("hbm", nproj * H * (Wf // 2) * c + L * nproj * (Wf - 1) * c),
         "grid": ("hbm", L * nproj * Wf * c + L * n0 * M2 * c),
         "colifft": ("hbm", L * n0 * M2 * c + L * n1 * n0 * c),
         "zusfft": ("hbm", L * n1 * n0 * c + n0 * n1 * n2 * 4),

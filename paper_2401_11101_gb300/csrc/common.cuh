@@ -157,13 +157,15 @@ int validate_dtype_kind(lamino_plan_t p, int dtype, int kind);
 int launch_rowfft(lamino_plan_t p, const void* d, int dtype, float2* R, int kind /* -1: no filter */,
                   cudaStream_t s, long row0 = 0, long row1 = -1);
 // Views of the Fourier form's two workspaces A and B (fourier_bufs). R, the
-// row spectra, and G, the plane-major half spectra (followed by the column
-// FFT's chunk statistics st), are whole; V holds the x1-pass planes of one
-// chunk of zc planes and P the deconvolved planes of all L planes.
+// row spectra (frequencies m >= 0 only, [nproj][H][Wf/2]), and G, the
+// plane-major half spectra (followed by the column FFT's chunk statistics
+// st), are whole; V holds the x1-pass planes of one chunk of zc planes and P
+// the deconvolved planes of all L planes.
 //   zc == L (no z chunking): A = R, then V [L][n0][M2]; B = G + st, then P.
 //   zc <  L: A = R, then P [L][n1][n0] followed by V [zc][n0][M2]; B = G + st
 //            (G must outlive every plane chunk).
-// The transpose (lamino_project) uses the same views in reverse order.
+// The transpose (lamino_project) uses the same views in reverse order, with
+// full row spectra in R ([nproj][H][Wf], the workspace is sized for them).
 struct FourierBufs {
     float2 *R, *G, *st, *V, *P;
     int CH;    // columns per column-FFT block = statistics chunk

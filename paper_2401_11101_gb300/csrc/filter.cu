@@ -72,9 +72,10 @@ __global__ void __launch_bounds__(MT, 1) k_filter(const Tin* __restrict__ d, flo
 
 // Fourier row pass. Optionally filters first (EP > 0: FFT of length Wp), then
 // places the W samples at offset offu of a length-Wf row, FFTs it, splits the
-// two real spectra and writes them in signed frequency order mi = m + Wf/2,
-// multiplied by the centring phase exp(2 pi i m cu/Wf) (zero at m = -Wf/2).
-// Output R[row][mi], row = k*H + r.
+// two real spectra and writes, multiplied by the centring phase
+// exp(2 pi i m cu/Wf), the frequencies m in [0, Wf/2) only: a real row's
+// spectrum at -m is the conjugate of that at m (and so is the phase), which
+// the column pass uses. Output R[row][m], row = k*H + r, pitch Wf/2.
 template <int EP, int EF, typename Tin, int MT>
 __global__ void __launch_bounds__(MT, 1) k_rowfft(const Tin* __restrict__ d, float2* __restrict__ R,
                                                 long row0, long row1, int W, int offu, FftDesc fp,
@@ -114,18 +115,16 @@ __global__ void __launch_bounds__(MT, 1) k_rowfft(const Tin* __restrict__ d, flo
     fft_run<EF>(SeqCP{xf}, ff, tid, active, -1.f);
     if (active) {
         const int half = Nf / 2;
-        for (int mi = tid; mi < Nf; mi += T) {
-            int m = mi - half;
-            int i1 = m < 0 ? m + Nf : m;          // index of +m
-            int i2 = m > 0 ? Nf - m : -m;         // index of -m
-            float2 Z = xf[fpad(i1)], Zc = xf[fpad(i2)];
+        for (int m = tid; m < half; m += T) {
+            const int i2 = m > 0 ? Nf - m : 0;    // index of -m
+            float2 Z = xf[fpad(m)], Zc = xf[fpad(i2)];
             Zc.y = -Zc.y;
             float2 A = make_float2(0.5f * (Z.x + Zc.x), 0.5f * (Z.y + Zc.y));
             float2 Dm = csub(Z, Zc);
             float2 B = make_float2(0.5f * Dm.y, -0.5f * Dm.x);   // (Z - conj Z(-m)) / (2i)
-            float2 ph = __ldg(phu + mi);
-            R[(size_t)rA * Nf + mi] = cmul(A, ph);
-            if (hasB) R[(size_t)rB * Nf + mi] = cmul(B, ph);
+            float2 ph = __ldg(phu + half + m);
+            R[(size_t)rA * half + m] = cmul(A, ph);
+            if (hasB) R[(size_t)rB * half + m] = cmul(B, ph);
         }
     }
 }
@@ -227,9 +226,9 @@ __global__ void __launch_bounds__(384) k_filter3(const Tin* __restrict__ d, floa
 // padded row are the filter's buffers shifted by o slots (zero past W). Then
 // the NF-point warp FFTs, the radix-3 step written back in natural order
 // (X[k + NF j] in buffer j, slot k), and the same epilogue as k_rowfft: the
-// two real spectra, the centring phase, R[row][m + Wf/2].
+// two real spectra, the centring phase, R[row][m] for m in [0, Wf/2).
 template <int N, int NF, typename Tin>
-__global__ void __launch_bounds__(384) k_rowfft3(const Tin* __restrict__ d, float2* __restrict__ R,
+__global__ void __launch_bounds__(384, 2) k_rowfft3(const Tin* __restrict__ d, float2* __restrict__ R,
                                                  long row0, long row1, int W, int offu,
                                                  const float2* __restrict__ twN, const float2* __restrict__ tw3N,
                                                  const float* __restrict__ filt,
@@ -277,18 +276,16 @@ __global__ void __launch_bounds__(384) k_rowfft3(const Tin* __restrict__ d, floa
     seq_sync(seq);
     constexpr int Nf = 3 * NF, half = Nf / 2;
     auto X = [&](int i) { return buf[(i / NF) * LB + i % NF]; };
-    for (int mi = t96; mi < Nf; mi += 96) {
-        const int m = mi - half;
-        const int i1 = m < 0 ? m + Nf : m;          // index of +m
-        const int i2 = m > 0 ? Nf - m : -m;         // index of -m
-        float2 Z = X(i1), Zc = X(i2);
+    for (int m = t96; m < half; m += 96) {
+        const int i2 = m > 0 ? Nf - m : 0;          // index of -m
+        float2 Z = X(m), Zc = X(i2);
         Zc.y = -Zc.y;
         const float2 A = make_float2(0.5f * (Z.x + Zc.x), 0.5f * (Z.y + Zc.y));
         const float2 Dm = csub(Z, Zc);
         const float2 B = make_float2(0.5f * Dm.y, -0.5f * Dm.x);   // (Z - conj Z(-m)) / (2i)
-        const float2 ph = __ldg(phu + mi);
-        R[(size_t)rA * Nf + mi] = cmul(A, ph);
-        if (hasB) R[(size_t)(rA + 1) * Nf + mi] = cmul(B, ph);
+        const float2 ph = __ldg(phu + half + m);
+        R[(size_t)rA * half + m] = cmul(A, ph);
+        if (hasB) R[(size_t)(rA + 1) * half + m] = cmul(B, ph);
     }
 }
 

@@ -3,8 +3,10 @@
 //   colfft  : second pass of the 2D FFT of every projection (along detector
 //             rows v), keeping the k_v >= 0 half of the spectrum and writing
 //             it plane-major: G[l][k][m]. Real projections make the planes
-//             -l the conjugates of planes l (the x3 pass uses 2 Re). Also
-//             writes per-chunk bounds of the values for the gridding.
+//             -l the conjugates of planes l (the x3 pass uses 2 Re), and the
+//             column -m the conjugate of the column m read backwards in k_v:
+//             one transform of each column m >= 0 gives both. Also writes
+//             per-chunk bounds of the values for the gridding.
 //   grid    : per k_v plane l and band of T2 rows of the oversampled x2 grid,
 //             Gaussian spreading of every point (k, m) at the frequency of
 //             Eq. uneqspace onto a shared-memory band of the 2x oversampled
@@ -34,10 +36,11 @@ __global__ void __launch_bounds__(512, 2) k_colfft(const float2* __restrict__ R,
                                                  int nproj, int H, int Wf, int L, int offv, FftDesc fh,
                                                  const float2* __restrict__ phv, int C) {
     extern __shared__ float2 sm[];
-    const int Hf = fh.n, ld = Hf + 1;
+    const int Hf = fh.n, ld = Hf + 1, half = Wf / 2;
     const int k = k0 + blockIdx.y, m0 = blockIdx.x * C;
-    // load C columns of projection k, zero-padded rows, into sequences of length Hf
-    // (8 independent loads in flight per thread)
+    // load the C columns m0 .. m0 + C - 1 (R holds m in [0, Wf/2)) of
+    // projection k, zero-padded rows, into sequences of length Hf (8
+    // independent loads in flight per thread)
     constexpr int U = 8;
     const int total = C * Hf;
     for (int base = threadIdx.x; base < total; base += U * blockDim.x) {
@@ -46,7 +49,7 @@ __global__ void __launch_bounds__(512, 2) k_colfft(const float2* __restrict__ R,
         for (int u = 0; u < U; ++u) {
             const int idx = base + u * blockDim.x;
             const int c = idx % C, r = idx / C - offv;
-            v[u] = (idx < total && r >= 0 && r < H) ? R[((size_t)k * H + r) * Wf + m0 + c]
+            v[u] = (idx < total && r >= 0 && r < H) ? R[((size_t)k * H + r) * half + m0 + c]
                                                     : make_float2(0.f, 0.f);
         }
 #pragma unroll
@@ -57,26 +60,46 @@ __global__ void __launch_bounds__(512, 2) k_colfft(const float2* __restrict__ R,
     }
     __syncthreads();
     fft_many<E>(sm, ld, C, fh, -1.f);
-    // write the half spectrum; keep it in shared memory for the statistics
+    // With S the transform of column m (slot j = k_v mod Hf):
+    //   G(m, l) = phv(l) S(l),  G(-m, l) = phv(l) conj S((Hf - l) mod Hf),
+    // since R(v, -m) = conj R(v, m). Write both halves (column 0 once) and
+    // keep them in shared memory for the statistics: G(m, l) in slot l,
+    // G(-m, l) in slot Hf - l (slot Hf is the sequence's pad). A thread reads
+    // and writes only its own two slots (L = Hf/2, so Hf - l > l).
     for (int idx = threadIdx.x; idx < C * L; idx += blockDim.x) {
-        const int c = idx % C, l = idx / C;
-        const float2 g = cmul(sm[c * ld + l], __ldg(phv + l));
-        G[((size_t)l * nproj + k) * Wf + m0 + c] = g;
-        sm[c * ld + l] = g;
+        const int c = idx % C, l = idx / C, m = m0 + c;
+        const float2 ph = __ldg(phv + l);
+        float2 sn = sm[c * ld + (l ? Hf - l : 0)];
+        sn.y = -sn.y;
+        const float2 gp = cmul(sm[c * ld + l], ph), gn = cmul(sn, ph);
+        float2* Gl = G + ((size_t)l * nproj + k) * Wf + half;
+        Gl[m] = gp;
+        if (m > 0) Gl[-m] = gn;
+        sm[c * ld + l] = gp;
+        sm[c * ld + Hf - l] = gn;
     }
     __syncthreads();
     // per plane, the sum and the maximum of max(|Re|, |Im|) over the block's C
-    // columns: the gridding kernel's bound on its fixed-point range.
-    // Layout st[k][m0 / C][l].
+    // columns m and over their C mirror columns -m: the gridding kernel's
+    // bound on its fixed-point range. Layout st[k][chunk][l], chunk m0 / C
+    // for the columns m >= 0 and nch + m0 / C for -m (nch = Wf / 2C).
+    const int nch = half / C;
     for (int l = threadIdx.x; l < L; l += blockDim.x) {
-        float sum = 0.f, mx = 0.f;
+        float sp = 0.f, mp = 0.f, sn = 0.f, mn = 0.f;
         for (int c = 0; c < C; ++c) {
             const float2 g = sm[c * ld + l];
             const float av = fmaxf(fabsf(g.x), fabsf(g.y));
-            sum += av;
-            mx = fmaxf(mx, av);
+            sp += av;
+            mp = fmaxf(mp, av);
+            if (m0 + c == 0) continue;               // column 0 is not a mirror
+            const float2 h = sm[c * ld + Hf - l];
+            const float an = fmaxf(fabsf(h.x), fabsf(h.y));
+            sn += an;
+            mn = fmaxf(mn, an);
         }
-        st[((size_t)k * (Wf / C) + m0 / C) * L + l] = make_float2(sum, mx);
+        float2* sk = st + (size_t)k * 2 * nch * L;
+        sk[(size_t)(m0 / C) * L + l] = make_float2(sp, mp);
+        sk[(size_t)(nch + m0 / C) * L + l] = make_float2(sn, mn);
     }
 }
 
@@ -232,6 +255,27 @@ constexpr int kRoundMagicBits = 0x4B400000;  // its bit pattern
 // points, from the column FFT's chunk statistics of every chunk that holds a
 // point of a line's intervals (lines k = threadIdx.x + j blockDim; per-thread
 // partial results).
+// Adds the chunk statistics (sum, max) of the m-interval [ms, me] of one line
+// (sl: the line's st rows, chunks ch wide, stride sstride): chunks m / ch of
+// its m >= 0 part and Wf / 2ch + (-m) / ch of its m < 0 part, as k_colfft
+// writes them.
+__device__ __forceinline__ void interval_stats(const float2* __restrict__ sl, int sstride, int Wf, int ch,
+                                               int ms, int me, float& ssum, float& smax) {
+    const int nch = Wf / (2 * ch);
+    if (me >= 0)
+        for (int c = max(ms, 0) / ch; c <= me / ch; ++c) {
+            const float2 v = __ldg(sl + (size_t)c * sstride);
+            ssum += v.x;
+            smax = fmaxf(smax, v.y);
+        }
+    if (ms < 0)
+        for (int c = max(1, -me) / ch; c <= -ms / ch; ++c) {
+            const float2 v = __ldg(sl + (size_t)(nch + c) * sstride);
+            ssum += v.x;
+            smax = fmaxf(smax, v.y);
+        }
+}
+
 __device__ __forceinline__ void band_stats(const float2* __restrict__ trig, int nproj, int Wf, int M2,
                                            float rho, float lo, float hi, const float2* __restrict__ st,
                                            int ch, int sstride, float& ssum, float& smax) {
@@ -242,12 +286,7 @@ __device__ __forceinline__ void band_stats(const float2* __restrict__ trig, int 
         const float AY = (float)M2 * cs.y / (float)Wf, BY = -(float)M2 * rho * cs.x;
         const int n = band_intervals(AY, BY, -half + 1, half - 1, lo, hi, M2, ms, me);
         const float2* sl = st + (size_t)k * (Wf / ch) * sstride;
-        for (int i = 0; i < n; ++i)
-            for (int c = (ms[i] + half) / ch; c <= (me[i] + half) / ch; ++c) {
-                const float2 v = __ldg(sl + (size_t)c * sstride);
-                ssum += v.x;
-                smax = fmaxf(smax, v.y);
-            }
+        for (int i = 0; i < n; ++i) interval_stats(sl, sstride, Wf, ch, ms[i], me[i], ssum, smax);
     }
 }
 
@@ -283,11 +322,7 @@ __device__ __forceinline__ int band_list(const float2* __restrict__ trig, int k0
                 // upper bound on the band's sum and maximum
                 const float2* sl = st + (size_t)k * (Wf / ch) * sstride;
                 for (int i = 0; i < nint[t]; ++i)
-                    for (int c = (ms[t][i] + half) / ch; c <= (me[t][i] + half) / ch; ++c) {
-                        const float2 v = __ldg(sl + (size_t)c * sstride);
-                        ssum += v.x;
-                        smax = fmaxf(smax, v.y);
-                    }
+                    interval_stats(sl, sstride, Wf, ch, ms[t][i], me[t][i], ssum, smax);
             }
         }
     }
@@ -851,11 +886,11 @@ int dispatch_grid_w(int w, const GridArgs& a, dim3 grid, int threads, size_t sme
 
 }  // namespace
 
-// Columns per block of the column FFT (a power of two dividing Wf, at most
+// Columns per block of the column FFT (a power of two dividing Wf/2, at most
 // 16, with the block's sequences within 100 KB of shared memory); also the
 // chunk of the statistics it writes for the gridding kernel.
 int colfft_chunk(lamino_plan_t p) {
-    int C = largest_pow2_divisor_upto(p->Wf, 16);
+    int C = largest_pow2_divisor_upto(p->Wf / 2, 16);
     while (C > 1 && (size_t)C * (p->Hf + 1) * sizeof(float2) > 100 * 1024) C /= 2;
     return C;
 }
@@ -887,7 +922,7 @@ FourierBufs fourier_bufs(lamino_plan_t p, void* a, void* b) {
     FourierBufs f;
     f.CH = colfft_chunk(p);
     f.zc = plane_chunk(p);
-    f.R = (float2*)a;                                        // [nproj][H][Wf]
+    f.R = (float2*)a;                                        // [nproj][H][Wf/2] (Rt: [nproj][H][Wf])
     f.G = (float2*)b;                                        // [L][nproj][Wf]
     f.st = f.G + (size_t)p->L * p->nproj * p->Wf;           // [nproj][Wf/CH][L]
     if (f.zc >= p->L) {
@@ -907,7 +942,7 @@ int launch_colfft(lamino_plan_t p, const FourierBufs& fb, int k0, int k1, cudaSt
     if (f.t > 512) return refuse_long_fft(p, f, "the column FFT (padded detector height)");
     const int C = fb.CH;
     size_t smem = (size_t)C * (f.n + 1) * sizeof(float2);
-    dim3 grid(p->Wf / C, k1 - k0);
+    dim3 grid(p->Wf / 2 / C, k1 - k0);         // the columns m >= 0 (R holds those)
     int threads = fft_block_threads(f, C);
     ProfScope prof(p, "colfft", s);
     if (f.e == 8) {
