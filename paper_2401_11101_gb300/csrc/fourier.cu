@@ -577,17 +577,23 @@ __global__ void __launch_bounds__(MT, MT > 512 ? 1 : 2) k_colifft(const float2* 
 }
 
 // ---------------------------------------------------------------- zusfft
-template <int E>
+// Row pitch (complex values) of the block's plane values [L][C]: C + 2 keeps
+// 16-byte rows and an odd number of 16-byte units per row, so the 16-byte
+// loads of a warp's consecutive planes spread over all banks.
+__host__ __device__ constexpr int zus_pitch(int C) { return C >= 2 ? C + 2 : 1; }
+
+template <int E, int CB>
 __global__ void __launch_bounds__(512, 2) k_zusfft(const float2* __restrict__ P, float* __restrict__ vol,
                                                  int L, int n0, int n1, int n2, FftDesc f3,
                                                  const int* __restrict__ zoff, const int* __restrict__ zl,
                                                  const float* __restrict__ zw,
-                                                 const float* __restrict__ dec3, int C, int i10) {
+                                                 const float* __restrict__ dec3, int i10) {
     extern __shared__ float2 sm[];
+    constexpr int C = CB, PP = zus_pitch(CB);
     const int M3 = f3.n, ld = M3 + 1;
     const int i1 = i10 + blockIdx.y, i00 = blockIdx.x * C;
-    float2* Pl = sm;                   // [L][C]
-    float2* U = sm + (size_t)L * C;    // [C][M3 + 1]
+    float2* Pl = sm;                    // [L][PP]
+    float2* U = sm + (size_t)L * PP;    // [C][M3 + 1]
     constexpr int NB = 8;
     const int total = C * L;
     for (int base = threadIdx.x; base < total; base += NB * blockDim.x) {
@@ -601,21 +607,37 @@ __global__ void __launch_bounds__(512, 2) k_zusfft(const float2* __restrict__ P,
 #pragma unroll
         for (int u = 0; u < NB; ++u) {
             const int idx = base + u * blockDim.x;
-            if (idx < total) Pl[idx] = v[u];
+            if (idx < total) Pl[(idx / C) * PP + idx % C] = v[u];
         }
     }
     __syncthreads();
-    for (int idx = threadIdx.x; idx < C * M3; idx += blockDim.x) {
-        int c = idx % C, s3 = idx / C;
-        float2 acc = make_float2(0.f, 0.f);
+    // gather onto the oversampled x3 grid: a thread per cell for all C
+    // columns, so every tap's (plane, weight) entry is read once per block
+    for (int s3 = threadIdx.x; s3 < M3; s3 += blockDim.x) {
+        float2 acc[C];
+#pragma unroll
+        for (int c = 0; c < C; ++c) acc[c] = make_float2(0.f, 0.f);
         const int b = __ldg(zoff + s3), e = __ldg(zoff + s3 + 1);
         for (int t = b; t < e; ++t) {
-            float wgt = __ldg(zw + t);
-            float2 v = Pl[__ldg(zl + t) * C + c];
-            acc.x = fmaf(wgt, v.x, acc.x);
-            acc.y = fmaf(wgt, v.y, acc.y);
+            const float wgt = __ldg(zw + t);
+            const float2* row = Pl + __ldg(zl + t) * PP;
+            if constexpr (C >= 2) {
+#pragma unroll
+                for (int j = 0; j < C / 2; ++j) {
+                    const float4 v = reinterpret_cast<const float4*>(row)[j];
+                    acc[2 * j].x = fmaf(wgt, v.x, acc[2 * j].x);
+                    acc[2 * j].y = fmaf(wgt, v.y, acc[2 * j].y);
+                    acc[2 * j + 1].x = fmaf(wgt, v.z, acc[2 * j + 1].x);
+                    acc[2 * j + 1].y = fmaf(wgt, v.w, acc[2 * j + 1].y);
+                }
+            } else {
+                const float2 v = row[0];
+                acc[0].x = fmaf(wgt, v.x, acc[0].x);
+                acc[0].y = fmaf(wgt, v.y, acc[0].y);
+            }
         }
-        U[c * ld + s3] = acc;
+#pragma unroll
+        for (int c = 0; c < C; ++c) U[c * ld + s3] = acc[c];
     }
     __syncthreads();
     fft_many<E>(U, ld, C, f3, +1.f);
@@ -1052,27 +1074,40 @@ int launch_colifft(lamino_plan_t p, const FourierBufs& fb, int l0, int l1, cudaS
     return LAMINO_OK;
 }
 
+template <int E, int CB>
+static void launch_zusfft_cb(lamino_plan_t p, const FourierBufs& fb, float* vol, int i10, dim3 grid,
+                             int threads, size_t smem, cudaStream_t s) {
+    set_smem(k_zusfft<E, CB>, smem);
+    k_zusfft<E, CB><<<grid, threads, smem, s>>>(fb.P, vol, p->L, p->n0, p->n1, p->n2, p->fM3, p->d_zoff,
+                                                 p->d_zl, p->d_zw, p->d_dec3, i10);
+}
+
+template <int E>
+static void dispatch_zusfft(int C, lamino_plan_t p, const FourierBufs& fb, float* vol, int i10, dim3 grid,
+                            int threads, size_t smem, cudaStream_t s) {
+    switch (C) {
+        case 16: launch_zusfft_cb<E, 16>(p, fb, vol, i10, grid, threads, smem, s); break;
+        case 8: launch_zusfft_cb<E, 8>(p, fb, vol, i10, grid, threads, smem, s); break;
+        case 4: launch_zusfft_cb<E, 4>(p, fb, vol, i10, grid, threads, smem, s); break;
+        case 2: launch_zusfft_cb<E, 2>(p, fb, vol, i10, grid, threads, smem, s); break;
+        default: launch_zusfft_cb<E, 1>(p, fb, vol, i10, grid, threads, smem, s); break;
+    }
+}
+
 int launch_zusfft(lamino_plan_t p, const FourierBufs& fb, float* vol, int i10, int i11, cudaStream_t s) {
     if (i11 <= i10) return LAMINO_OK;
     // x3 USFFT of the columns of x2 rows [i10, i11)
     const FftDesc& f = p->fM3;
     if (f.t > 512) return refuse_long_fft(p, f, "the x3 USFFT");
     int C = 16;
-    auto bytes = [&](int c) { return (size_t)c * ((size_t)p->L + f.n + 1) * sizeof(float2); };
+    auto bytes = [&](int c) { return ((size_t)zus_pitch(c) * p->L + (size_t)c * (f.n + 1)) * sizeof(float2); };
     while (C > 1 && bytes(C) > 72 * 1024) C /= 2;
     size_t smem = bytes(C);
     dim3 grid((p->n0 + C - 1) / C, i11 - i10);
     int threads = fft_block_threads(f, C);
     ProfScope prof(p, "zusfft", s);
-    if (f.e == 8) {
-        set_smem(k_zusfft<8>, smem);
-        k_zusfft<8><<<grid, threads, smem, s>>>(fb.P, vol, p->L, p->n0, p->n1, p->n2, f, p->d_zoff,
-                                                 p->d_zl, p->d_zw, p->d_dec3, C, i10);
-    } else {
-        set_smem(k_zusfft<12>, smem);
-        k_zusfft<12><<<grid, threads, smem, s>>>(fb.P, vol, p->L, p->n0, p->n1, p->n2, f, p->d_zoff,
-                                                  p->d_zl, p->d_zw, p->d_dec3, C, i10);
-    }
+    if (f.e == 8) dispatch_zusfft<8>(C, p, fb, vol, i10, grid, threads, smem, s);
+    else dispatch_zusfft<12>(C, p, fb, vol, i10, grid, threads, smem, s);
     LAM_LAUNCH_CHECK(p, "x3 USFFT kernel");
     return LAMINO_OK;
 }
