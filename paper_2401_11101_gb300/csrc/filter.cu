@@ -155,17 +155,27 @@ __device__ __forceinline__ void seq_sync(int seq) {
 }
 
 // Rows rA and rA + 1 (if hasB) placed at offset `off` of a length-3NB row,
-// 3-way decimated into buf (buffers LB apart), zero elsewhere.
+// 3-way decimated into buf (buffers LB apart), zero elsewhere. Sixteen loads
+// of a thread are in flight at a time.
 template <typename Tin>
 __device__ __forceinline__ void load_rows3(const Tin* __restrict__ d, float2* buf, int LB, int NB,
                                            long rA, bool hasB, int W, int off, int t96) {
+    constexpr int U = 8;
     const size_t ra = (size_t)rA * W, rb = ra + W;
-    for (int j = t96; j < 3 * NB; j += 96) {
-        const int src = j - off;
-        const bool in = src >= 0 && src < W;
-        const float a = in ? load_f(d, ra + src) : 0.f;
-        const float b = (in && hasB) ? load_f(d, rb + src) : 0.f;
-        buf[(j % 3) * LB + j / 3] = make_float2(a, b);
+    for (int j0 = t96; j0 < 3 * NB; j0 += U * 96) {
+        float a[U], b[U];
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+            const int j = j0 + u * 96, src = j - off;
+            const bool in = j < 3 * NB && src >= 0 && src < W;
+            a[u] = in ? load_f(d, ra + src) : 0.f;
+            b[u] = (in && hasB) ? load_f(d, rb + src) : 0.f;
+        }
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+            const int j = j0 + u * 96;
+            if (j < 3 * NB) buf[(j % 3) * LB + j / 3] = make_float2(a[u], b[u]);
+        }
     }
 }
 
