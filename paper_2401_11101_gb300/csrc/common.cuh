@@ -34,6 +34,21 @@ struct FftDesc {
     const float2* tw = nullptr;  // device table exp(-2 pi i s/n), s in [0, n)
 };
 
+// Quotient and remainder by a divisor d >= 1 fixed at launch, for dividends
+// 0 <= n with n d < 2^32, by one high multiply with M = ceil(2^32 / d):
+// n M / 2^32 = n/d + n e / (d 2^32) with e = M d - 2^32 in [0, d), and the
+// second term is below n / 2^32 < 1/d, so the floor stays floor(n/d). The
+// kernels' index loops divide by launch-time sizes (columns per block, grid
+// lengths), where a division by a runtime value costs ~20 instructions.
+struct FastDiv {
+    unsigned M = 0;
+    int d = 1;
+    FastDiv() = default;
+    explicit FastDiv(int dd) : M(dd > 1 ? (unsigned)((0x100000000ull + (unsigned)dd - 1) / (unsigned)dd) : 0u), d(dd) {}
+    __device__ __forceinline__ int div(int n) const { return d == 1 ? n : (int)__umulhi((unsigned)n, M); }
+    __device__ __forceinline__ int mod(int n) const { return n - div(n) * d; }
+};
+
 // Elements per thread: 8 for 2^k lengths (radix-8 stages, one radix-4/2), 12
 // for 3*2^k lengths (radix-4/2 stages and one radix-3 stage).
 int fft_elems(int n);

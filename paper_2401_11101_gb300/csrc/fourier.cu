@@ -34,8 +34,9 @@ template <int E>
 __global__ void __launch_bounds__(512, 2) k_colfft(const float2* __restrict__ R, float2* __restrict__ G,
                                                  float2* __restrict__ st, int k0,
                                                  int nproj, int H, int Wf, int L, int offv, FftDesc fh,
-                                                 const float2* __restrict__ phv, int C) {
+                                                 const float2* __restrict__ phv, FastDiv fC) {
     extern __shared__ float2 sm[];
+    const int C = fC.d;
     const int Hf = fh.n, ld = Hf + 1, half = Wf / 2;
     const int k = k0 + blockIdx.y, m0 = blockIdx.x * C;
     // load the C columns m0 .. m0 + C - 1 (R holds m in [0, Wf/2)) of
@@ -48,14 +49,15 @@ __global__ void __launch_bounds__(512, 2) k_colfft(const float2* __restrict__ R,
 #pragma unroll
         for (int u = 0; u < U; ++u) {
             const int idx = base + u * blockDim.x;
-            const int c = idx % C, r = idx / C - offv;
+            const int q = fC.div(idx), c = idx - q * C, r = q - offv;
             v[u] = (idx < total && r >= 0 && r < H) ? R[((size_t)k * H + r) * half + m0 + c]
                                                     : make_float2(0.f, 0.f);
         }
 #pragma unroll
         for (int u = 0; u < U; ++u) {
             const int idx = base + u * blockDim.x;
-            if (idx < total) sm[(idx % C) * ld + idx / C] = v[u];
+            const int q = fC.div(idx);
+            if (idx < total) sm[(idx - q * C) * ld + q] = v[u];
         }
     }
     __syncthreads();
@@ -67,7 +69,7 @@ __global__ void __launch_bounds__(512, 2) k_colfft(const float2* __restrict__ R,
     // G(-m, l) in slot Hf - l (slot Hf is the sequence's pad). A thread reads
     // and writes only its own two slots (L = Hf/2, so Hf - l > l).
     for (int idx = threadIdx.x; idx < C * L; idx += blockDim.x) {
-        const int c = idx % C, l = idx / C, m = m0 + c;
+        const int l = fC.div(idx), c = idx - l * C, m = m0 + c;
         const float2 ph = __ldg(phv + l);
         float2 sn = sm[c * ld + (l ? Hf - l : 0)];
         sn.y = -sn.y;
@@ -111,6 +113,7 @@ struct GridArgs {
     const float2* trig;
     const float* dec1;
     int nproj, Wf, Hf, n0, M1, M2, T2, ld;   // ld: row pitch of the band accumulator
+    FastDiv fT2, fNR;                        // division by T2 and by the transpose's rows T2 + 2W - 1
     int ch;                                  // column chunk of the statistics
     int L, l0;                               // planes of the half spectrum; first plane of
                                              // the launch (blockIdx.y = l - l0; V is [l - l0])
@@ -532,7 +535,7 @@ __global__ void __launch_bounds__(1024, 1) k_grid(GridArgs a) {
     // crop x1 in [-n0/2, n0/2), deconvolve, write V[l][i0][s2] (s2 fastest)
     const int n0 = a.n0;
     for (int idx = threadIdx.x; idx < T2 * n0; idx += blockDim.x) {
-        int rr = idx % T2, i0 = idx / T2;
+        const int i0 = a.fT2.div(idx), rr = idx - i0 * T2;
         int s1 = i0 - n0 / 2;
         s1 += (s1 < 0) ? M1 : 0;
         s1 = fft_planar_pos<E>(a.f1, s1, true);
@@ -545,8 +548,10 @@ __global__ void __launch_bounds__(1024, 1) k_grid(GridArgs a) {
 template <int E, int MT>
 __global__ void __launch_bounds__(MT, MT > 512 ? 1 : 2) k_colifft(const float2* __restrict__ V, float2* __restrict__ P,
                                                   int n0, int n1, FftDesc f2,
-                                                  const float* __restrict__ dec2, int C, int l0) {
+                                                  const float* __restrict__ dec2, FastDiv fC, FastDiv fM2,
+                                                  int l0) {
     extern __shared__ float2 sm[];
+    const int C = fC.d;
     const int M2 = f2.n, ld = M2 + 1;
     const int lv = blockIdx.y, l = l0 + lv, i00 = blockIdx.x * C;   // V holds planes [l0, ...)
     constexpr int U = 8;
@@ -556,19 +561,20 @@ __global__ void __launch_bounds__(MT, MT > 512 ? 1 : 2) k_colifft(const float2* 
 #pragma unroll
         for (int u = 0; u < U; ++u) {
             const int idx = base + u * blockDim.x;
-            const int i0 = i00 + idx / M2;
-            v[u] = (idx < total && i0 < n0) ? V[((size_t)lv * n0 + i0) * M2 + idx % M2] : make_float2(0.f, 0.f);
+            const int q = fM2.div(idx), i0 = i00 + q;
+            v[u] = (idx < total && i0 < n0) ? V[((size_t)lv * n0 + i0) * M2 + (idx - q * M2)] : make_float2(0.f, 0.f);
         }
 #pragma unroll
         for (int u = 0; u < U; ++u) {
             const int idx = base + u * blockDim.x;
-            if (idx < total) sm[(idx / M2) * ld + idx % M2] = v[u];
+            const int q = fM2.div(idx);
+            if (idx < total) sm[q * ld + (idx - q * M2)] = v[u];
         }
     }
     __syncthreads();
     fft_many<E>(sm, ld, C, f2, +1.f);
     for (int idx = threadIdx.x; idx < C * n1; idx += blockDim.x) {
-        int c = idx % C, i1 = idx / C, i0 = i00 + c;
+        const int i1 = fC.div(idx), c = idx - i1 * C, i0 = i00 + c;
         if (i0 >= n0) continue;
         int s2 = i1 - n1 / 2;
         s2 += (s2 < 0) ? M2 : 0;
@@ -682,14 +688,15 @@ template <int E>
 __global__ void __launch_bounds__(512, 2) k_zusfft_t(const float* __restrict__ vol, float2* __restrict__ Pt,
                                                      int L, int n0, int n1, int n2, FftDesc f3,
                                                      const int2* __restrict__ ztap, int wz,
-                                                     const float* __restrict__ dec3, int C) {
+                                                     const float* __restrict__ dec3, FastDiv fC) {
     extern __shared__ float2 sm[];
+    const int C = fC.d;
     const int M3 = f3.n, ld = M3 + 1;
     const int i1 = blockIdx.y, i00 = blockIdx.x * C;
     for (int i = threadIdx.x; i < C * ld; i += blockDim.x) sm[i] = make_float2(0.f, 0.f);
     __syncthreads();
     for (int idx = threadIdx.x; idx < C * n2; idx += blockDim.x) {
-        const int c = idx % C, i2 = idx / C, i0 = i00 + c;
+        const int i2 = fC.div(idx), c = idx - i2 * C, i0 = i00 + c;
         int s3 = i2 - n2 / 2;
         s3 += (s3 < 0) ? M3 : 0;
         const float v = (i0 < n0) ? vol[((size_t)i2 * n1 + i1) * n0 + i0] * __ldg(dec3 + i2) : 0.f;
@@ -698,7 +705,7 @@ __global__ void __launch_bounds__(512, 2) k_zusfft_t(const float* __restrict__ v
     __syncthreads();
     fft_many<E>(sm, ld, C, f3, -1.f);
     for (int idx = threadIdx.x; idx < C * L; idx += blockDim.x) {
-        const int c = idx % C, l = idx / C, i0 = i00 + c;
+        const int l = fC.div(idx), c = idx - l * C, i0 = i00 + c;
         if (i0 >= n0) continue;
         float2 acc = make_float2(0.f, 0.f);
         for (int t = 0; t < 2 * wz; ++t) {
@@ -716,14 +723,16 @@ __global__ void __launch_bounds__(512, 2) k_zusfft_t(const float* __restrict__ v
 template <int E>
 __global__ void __launch_bounds__(512, 2) k_colifft_t(const float2* __restrict__ Pt, float2* __restrict__ Vt,
                                                       int n0, int n1, FftDesc f2,
-                                                      const float* __restrict__ dec2, int C, int l0) {
+                                                      const float* __restrict__ dec2, FastDiv fC, FastDiv fM2,
+                                                      int l0) {
     extern __shared__ float2 sm[];
+    const int C = fC.d;
     const int M2 = f2.n, ld = M2 + 1;
     const int lv = blockIdx.y, l = l0 + lv, i00 = blockIdx.x * C;   // Vt holds planes [l0, ...)
     for (int i = threadIdx.x; i < C * ld; i += blockDim.x) sm[i] = make_float2(0.f, 0.f);
     __syncthreads();
     for (int idx = threadIdx.x; idx < C * n1; idx += blockDim.x) {
-        const int c = idx % C, i1 = idx / C, i0 = i00 + c;
+        const int i1 = fC.div(idx), c = idx - i1 * C, i0 = i00 + c;
         int s2 = i1 - n1 / 2;
         s2 += (s2 < 0) ? M2 : 0;
         sm[c * ld + s2] = (i0 < n0) ? cscale(Pt[((size_t)l * n1 + i1) * n0 + i0], __ldg(dec2 + i1))
@@ -732,7 +741,7 @@ __global__ void __launch_bounds__(512, 2) k_colifft_t(const float2* __restrict__
     __syncthreads();
     fft_many<E>(sm, ld, C, f2, -1.f);
     for (int idx = threadIdx.x; idx < C * M2; idx += blockDim.x) {
-        const int c = idx / M2, s = idx % M2, i0 = i00 + c;
+        const int c = fM2.div(idx), s = idx - c * M2, i0 = i00 + c;
         if (i0 < n0) Vt[((size_t)lv * n0 + i0) * M2 + s] = sm[c * ld + s];
     }
 }
@@ -759,7 +768,7 @@ __global__ void __launch_bounds__(512, 1) k_grid_t(GridArgs a, const float2* __r
     for (int i = threadIdx.x; i < NR * ld; i += blockDim.x) X[i] = make_float2(0.f, 0.f);
     __syncthreads();
     for (int idx = threadIdx.x; idx < NR * n0; idx += blockDim.x) {
-        const int rr = idx % NR, i0 = idx / NR;
+        const int i0 = a.fNR.div(idx), rr = idx - i0 * NR;
         int s2 = s20 + rr;
         s2 -= (s2 >= M2) ? M2 : 0;
         int s1 = i0 - n0 / 2;
@@ -831,12 +840,13 @@ __global__ void __launch_bounds__(512, 1) k_grid_t(GridArgs a, const float2* __r
 template <int E>
 __global__ void __launch_bounds__(512, 2) k_colfft_t(const float2* __restrict__ Gt, float2* __restrict__ Rt,
                                                      int nproj, int H, int Wf, int L, int offv, FftDesc fh,
-                                                     const float2* __restrict__ phv, int C) {
+                                                     const float2* __restrict__ phv, FastDiv fC) {
     extern __shared__ float2 sm[];
+    const int C = fC.d;
     const int Hf = fh.n, ld = Hf + 1;
     const int k = blockIdx.y, m0 = blockIdx.x * C;
     for (int idx = threadIdx.x; idx < C * Hf; idx += blockDim.x) {
-        const int c = idx % C, l = idx / C;
+        const int l = fC.div(idx), c = idx - l * C;
         float2 v = make_float2(0.f, 0.f);
         if (l < L) {
             float2 ph = __ldg(phv + l);
@@ -848,7 +858,7 @@ __global__ void __launch_bounds__(512, 2) k_colfft_t(const float2* __restrict__ 
     __syncthreads();
     fft_many<E>(sm, ld, C, fh, +1.f);
     for (int idx = threadIdx.x; idx < C * H; idx += blockDim.x) {
-        const int c = idx % C, r = idx / C;
+        const int r = fC.div(idx), c = idx - r * C;
         Rt[((size_t)k * H + r) * Wf + m0 + c] = sm[c * ld + r + offv];
     }
 }
@@ -970,11 +980,11 @@ int launch_colfft(lamino_plan_t p, const FourierBufs& fb, int k0, int k1, cudaSt
     if (f.e == 8) {
         set_smem(k_colfft<8>, smem);
         k_colfft<8><<<grid, threads, smem, s>>>(fb.R, fb.G, fb.st, k0, p->nproj, p->H, p->Wf, p->L, p->offv, f,
-                                                 p->d_phv, C);
+                                                 p->d_phv, FastDiv(C));
     } else {
         set_smem(k_colfft<12>, smem);
         k_colfft<12><<<grid, threads, smem, s>>>(fb.R, fb.G, fb.st, k0, p->nproj, p->H, p->Wf, p->L, p->offv, f,
-                                                  p->d_phv, C);
+                                                  p->d_phv, FastDiv(C));
     }
     LAM_LAUNCH_CHECK(p, "column FFT kernel");
     return LAMINO_OK;
@@ -1026,6 +1036,7 @@ int launch_grid(lamino_plan_t p, const FourierBufs& fb, int l0, int l1, cudaStre
     while (T2 > 1 && (size_t)T2 * a.ld * sizeof(float2) > 132 * 1024) T2 /= 2;
     while (p->M2 % T2) T2 /= 2;
     a.T2 = T2;
+    a.fT2 = FastDiv(T2);
     // band accumulator (planar) + compact interval list + per-line counts, for
     // chunks of lines when every line's list does not fit beside the band
     if (p->Wf > 8192) return fail(p, LAMINO_EUNSUPPORTED, "gridding supports Wf <= 8192");
@@ -1065,7 +1076,7 @@ int launch_colifft(lamino_plan_t p, const FourierBufs& fb, int l0, int l1, cudaS
     ProfScope prof(p, "colifft", s);
     auto go = [&](auto kern) {
         set_smem(kern, smem);
-        kern<<<grid, threads, smem, s>>>(fb.V, fb.P, p->n0, p->n1, f, p->d_dec2, C, l0);
+        kern<<<grid, threads, smem, s>>>(fb.V, fb.P, p->n0, p->n1, f, p->d_dec2, FastDiv(C), FastDiv(f.n), l0);
     };
     if (threads > 512) go(k_colifft<8, 1024>);          // 8192-point x2 grids
     else if (f.e == 8) go(k_colifft<8, 512>);
@@ -1158,10 +1169,11 @@ int launch_project_fourier(lamino_plan_t p, const FourierBufs& fb, const float* 
         ProfScope prof(p, "zusfft_t", s);
         if (f.e == 8) {
             set_smem(k_zusfft_t<8>, smem);
-            k_zusfft_t<8><<<grid, threads, smem, s>>>(vol, Pt, p->L, p->n0, p->n1, p->n2, f, p->d_ztap, p->wz, p->d_dec3, C);
+            k_zusfft_t<8><<<grid, threads, smem, s>>>(vol, Pt, p->L, p->n0, p->n1, p->n2, f, p->d_ztap, p->wz, p->d_dec3, FastDiv(C));
         } else {
             set_smem(k_zusfft_t<12>, smem);
-            k_zusfft_t<12><<<grid, threads, smem, s>>>(vol, Pt, p->L, p->n0, p->n1, p->n2, f, p->d_ztap, p->wz, p->d_dec3, C);
+            k_zusfft_t<12><<<grid, threads, smem, s>>>(vol, Pt, p->L, p->n0, p->n1, p->n2, f, p->d_ztap, p->wz, p->d_dec3,
+                                                        FastDiv(C));
         }
         LAM_LAUNCH_CHECK(p, "x3 USFFT transpose kernel");
     }
@@ -1171,6 +1183,7 @@ int launch_project_fourier(lamino_plan_t p, const FourierBufs& fb, const float* 
     while (T2 > 1 && (size_t)(T2 + 2 * p->w - 1) * a.ld * sizeof(float2) > 150 * 1024) T2 /= 2;
     while (p->M2 % T2) T2 /= 2;
     a.T2 = T2;
+    a.fNR = FastDiv(T2 + 2 * p->w - 1);
     const size_t tile = (size_t)(T2 + 2 * p->w - 1) * a.ld * sizeof(float2);
     a.lchunk = line_chunk(p->nproj, tile, 4 * 512);
     if (a.lchunk <= 0)
@@ -1187,10 +1200,12 @@ int launch_project_fourier(lamino_plan_t p, const FourierBufs& fb, const float* 
             ProfScope prof(p, "colifft_t", s);
             if (f.e == 8) {
                 set_smem(k_colifft_t<8>, smem);
-                k_colifft_t<8><<<grid, threads, smem, s>>>(Pt, Vt, p->n0, p->n1, f, p->d_dec2, C, l0);
+                k_colifft_t<8><<<grid, threads, smem, s>>>(Pt, Vt, p->n0, p->n1, f, p->d_dec2, FastDiv(C),
+                                                           FastDiv(f.n), l0);
             } else {
                 set_smem(k_colifft_t<12>, smem);
-                k_colifft_t<12><<<grid, threads, smem, s>>>(Pt, Vt, p->n0, p->n1, f, p->d_dec2, C, l0);
+                k_colifft_t<12><<<grid, threads, smem, s>>>(Pt, Vt, p->n0, p->n1, f, p->d_dec2, FastDiv(C),
+                                                            FastDiv(f.n), l0);
             }
             LAM_LAUNCH_CHECK(p, "x2 FFT transpose kernel");
         }
@@ -1225,10 +1240,12 @@ int launch_project_fourier(lamino_plan_t p, const FourierBufs& fb, const float* 
         ProfScope prof(p, "colfft_t", s);
         if (f.e == 8) {
             set_smem(k_colfft_t<8>, smem);
-            k_colfft_t<8><<<grid, threads, smem, s>>>(Gt, Rt, p->nproj, p->H, p->Wf, p->L, p->offv, f, p->d_phv, C);
+            k_colfft_t<8><<<grid, threads, smem, s>>>(Gt, Rt, p->nproj, p->H, p->Wf, p->L, p->offv, f, p->d_phv,
+                                                      FastDiv(C));
         } else {
             set_smem(k_colfft_t<12>, smem);
-            k_colfft_t<12><<<grid, threads, smem, s>>>(Gt, Rt, p->nproj, p->H, p->Wf, p->L, p->offv, f, p->d_phv, C);
+            k_colfft_t<12><<<grid, threads, smem, s>>>(Gt, Rt, p->nproj, p->H, p->Wf, p->L, p->offv, f, p->d_phv,
+                                                       FastDiv(C));
         }
         LAM_LAUNCH_CHECK(p, "column FFT transpose kernel");
     }
