@@ -265,18 +265,22 @@ constexpr int kRoundMagicBits = 0x4B400000;  // its bit pattern
 __device__ __forceinline__ void interval_stats(const float2* __restrict__ sl, int sstride, int Wf, int ch,
                                                int ms, int me, float& ssum, float& smax) {
     const int nch = Wf / (2 * ch);
-    if (me >= 0)
-        for (int c = max(ms, 0) / ch; c <= me / ch; ++c) {
-            const float2 v = __ldg(sl + (size_t)c * sstride);
-            ssum += v.x;
-            smax = fmaxf(smax, v.y);
+    // chunks c0 .. c1 of the rows from off on: eight loads in flight at a time
+    auto add = [&](int c0, int c1, int off) {
+        for (int c = c0; c <= c1; c += 8) {
+            float2 v[8];
+#pragma unroll
+            for (int u = 0; u < 8; ++u)
+                v[u] = (c + u <= c1) ? __ldg(sl + (size_t)(off + c + u) * sstride) : make_float2(0.f, 0.f);
+#pragma unroll
+            for (int u = 0; u < 8; ++u) {
+                ssum += v[u].x;
+                smax = fmaxf(smax, v[u].y);
+            }
         }
-    if (ms < 0)
-        for (int c = max(1, -me) / ch; c <= -ms / ch; ++c) {
-            const float2 v = __ldg(sl + (size_t)(nch + c) * sstride);
-            ssum += v.x;
-            smax = fmaxf(smax, v.y);
-        }
+    };
+    if (me >= 0) add(max(ms, 0) / ch, me / ch, 0);
+    if (ms < 0) add(max(1, -me) / ch, -ms / ch, nch);
 }
 
 __device__ __forceinline__ void band_stats(const float2* __restrict__ trig, int nproj, int Wf, int M2,
