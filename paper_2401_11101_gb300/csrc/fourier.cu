@@ -29,6 +29,14 @@
 namespace lam {
 namespace {
 
+// Pitch (complex values) of the C sequences of length n of the x2 and x3
+// passes: ld = 16/C (mod 16), so that when a half-warp reads element s (and
+// s + 1, ...) of C consecutive sequences (lanes c = 0..C-1 over 16/C
+// consecutive s), the 8-byte slots c ld + s fall on 16 different bank pairs.
+__host__ __device__ constexpr int seq_pitch(int n, int C) {
+    return n + ((((16 / C) - n) % 16 + 16) % 16 == 0 ? 16 : (((16 / C) - n) % 16 + 16) % 16);
+}
+
 // ---------------------------------------------------------------- colfft
 template <int E>
 __global__ void __launch_bounds__(512, 2) k_colfft(const float2* __restrict__ R, float2* __restrict__ G,
@@ -556,7 +564,7 @@ __global__ void __launch_bounds__(MT, MT > 512 ? 1 : 2) k_colifft(const float2* 
                                                   int l0) {
     extern __shared__ float2 sm[];
     const int C = fC.d;
-    const int M2 = f2.n, ld = M2 + 1;
+    const int M2 = f2.n, ld = seq_pitch(M2, C);
     const int lv = blockIdx.y, l = l0 + lv, i00 = blockIdx.x * C;   // V holds planes [l0, ...)
     constexpr int U = 8;
     const int total = C * M2;
@@ -600,7 +608,7 @@ __global__ void __launch_bounds__(512, 2) k_zusfft(const float2* __restrict__ P,
                                                  const float* __restrict__ dec3, int i10) {
     extern __shared__ float2 sm[];
     constexpr int C = CB, PP = zus_pitch(CB);
-    const int M3 = f3.n, ld = M3 + 1;
+    const int M3 = f3.n, ld = seq_pitch(M3, C);
     const int i1 = i10 + blockIdx.y, i00 = blockIdx.x * C;
     float2* Pl = sm;                    // [L][PP]
     float2* U = sm + (size_t)L * PP;    // [C][M3 + 1]
@@ -1065,7 +1073,7 @@ int launch_grid(lamino_plan_t p, const FourierBufs& fb, int l0, int l1, cudaStre
 // blocks share an SM and one block's loads overlap another's FFT.
 static int x2_chunk(const FftDesc& f) {
     int C = 16;
-    while (C > 1 && (size_t)C * (f.n + 1) * sizeof(float2) > 72 * 1024) C /= 2;
+    while (C > 1 && (size_t)C * seq_pitch(f.n, C) * sizeof(float2) > 72 * 1024) C /= 2;
     return C;
 }
 
@@ -1074,7 +1082,7 @@ int launch_colifft(lamino_plan_t p, const FourierBufs& fb, int l0, int l1, cudaS
     // x2 inverse FFT of planes [l0, l1): V (chunk-relative) -> P (absolute)
     const FftDesc& f = p->fM2;
     const int C = x2_chunk(f);
-    size_t smem = (size_t)C * (f.n + 1) * sizeof(float2);
+    size_t smem = (size_t)C * seq_pitch(f.n, C) * sizeof(float2);
     dim3 grid((p->n0 + C - 1) / C, l1 - l0);
     int threads = fft_block_threads(f, C);
     ProfScope prof(p, "colifft", s);
@@ -1115,7 +1123,7 @@ int launch_zusfft(lamino_plan_t p, const FourierBufs& fb, float* vol, int i10, i
     const FftDesc& f = p->fM3;
     if (f.t > 512) return refuse_long_fft(p, f, "the x3 USFFT");
     int C = 16;
-    auto bytes = [&](int c) { return ((size_t)zus_pitch(c) * p->L + (size_t)c * (f.n + 1)) * sizeof(float2); };
+    auto bytes = [&](int c) { return ((size_t)zus_pitch(c) * p->L + (size_t)c * seq_pitch(f.n, c)) * sizeof(float2); };
     while (C > 1 && bytes(C) > 72 * 1024) C /= 2;
     size_t smem = bytes(C);
     dim3 grid((p->n0 + C - 1) / C, i11 - i10);
