@@ -93,6 +93,8 @@ struct lamino_plan_s {
     int* d_zoff = nullptr;         // [M3+1] CSR offsets of the x3 gridding table
     int* d_zl = nullptr;           // taps: plane index
     float* d_zw = nullptr;         // taps: weight (Gaussian x Hermitian factor)
+    int2* d_zrange = nullptr;      // [M3] (first plane, taps) of each cell when its planes are consecutive
+    float* d_zwt = nullptr;        // [zmax][M3] the same weights tap-major (d_zrange set only then)
     int2* d_ztap = nullptr;        // [L][2 wz] (cell, weight bits) per plane: the same taps by plane
     float2* d_tw = nullptr;        // all FFT twiddle tables
     int* d_err = nullptr;          // device error word (bounded waits)

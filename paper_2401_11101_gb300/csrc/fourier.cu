@@ -605,6 +605,7 @@ __global__ void __launch_bounds__(512, 2) k_zusfft(const float2* __restrict__ P,
                                                  int L, int n0, int n1, int n2, FftDesc f3,
                                                  const int* __restrict__ zoff, const int* __restrict__ zl,
                                                  const float* __restrict__ zw,
+                                                 const int2* __restrict__ zrange, const float* __restrict__ zwt,
                                                  const float* __restrict__ dec3, int i10) {
     extern __shared__ float2 sm[];
     constexpr int C = CB, PP = zus_pitch(CB);
@@ -635,10 +636,21 @@ __global__ void __launch_bounds__(512, 2) k_zusfft(const float2* __restrict__ P,
         float2 acc[C];
 #pragma unroll
         for (int c = 0; c < C; ++c) acc[c] = make_float2(0.f, 0.f);
-        const int b = __ldg(zoff + s3), e = __ldg(zoff + s3 + 1);
-        for (int t = b; t < e; ++t) {
-            const float wgt = __ldg(zw + t);
-            const float2* row = Pl + __ldg(zl + t) * PP;
+        // taps: planes l0 .. l0 + n - 1 with weights zwt[t][s3] (coalesced
+        // across the warp's cells), else the CSR list of the cell
+        int t0, n, l0 = 0;
+        if (zrange) {
+            const int2 r = __ldg(zrange + s3);
+            t0 = 0;
+            n = r.y;
+            l0 = r.x;
+        } else {
+            t0 = __ldg(zoff + s3);
+            n = __ldg(zoff + s3 + 1) - t0;
+        }
+        for (int t = 0; t < n; ++t) {
+            const float wgt = zrange ? __ldg(zwt + (size_t)t * M3 + s3) : __ldg(zw + t0 + t);
+            const float2* row = Pl + (zrange ? l0 + t : __ldg(zl + t0 + t)) * PP;
             if constexpr (C >= 2) {
 #pragma unroll
                 for (int j = 0; j < C / 2; ++j) {
@@ -1102,7 +1114,7 @@ static void launch_zusfft_cb(lamino_plan_t p, const FourierBufs& fb, float* vol,
                              int threads, size_t smem, cudaStream_t s) {
     set_smem(k_zusfft<E, CB>, smem);
     k_zusfft<E, CB><<<grid, threads, smem, s>>>(fb.P, vol, p->L, p->n0, p->n1, p->n2, p->fM3, p->d_zoff,
-                                                 p->d_zl, p->d_zw, p->d_dec3, i10);
+                                                 p->d_zl, p->d_zw, p->d_zrange, p->d_zwt, p->d_dec3, i10);
 }
 
 template <int E>

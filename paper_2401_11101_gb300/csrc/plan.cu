@@ -241,7 +241,8 @@ int upload(lamino_plan_t p, T** dst, const std::vector<T>& v, const char* what) 
 
 void free_plan(lamino_plan_t p) {
     void* bufs[] = {p->d_trig, p->d_trig64, p->d_filt, p->d_phu, p->d_phv, p->d_dec1,
-                    p->d_dec2, p->d_dec3, p->d_zoff, p->d_zl, p->d_zw, p->d_ztap, p->d_tw, p->d_err,
+                    p->d_dec2, p->d_dec3, p->d_zoff, p->d_zl, p->d_zw, p->d_zrange, p->d_zwt,
+                    p->d_ztap, p->d_tw, p->d_err,
                     p->ws_a, p->ws_b, p->q_buf, p->q_pad, p->h_in, p->h_vol};
     for (void* b : bufs)
         if (b) cudaFree(b);
@@ -374,6 +375,24 @@ int build_tables(lamino_plan_t p) {
     }
     zoff[p->M3] = (int)zl.size();
     p->zmax = zmax;
+    // When every cell's planes are consecutive (always but for x3 grids of a
+    // few cells, where a cell can see both images of the periodic grid), the
+    // x3 pass reads (first plane, count) per cell and the weights tap-major,
+    // so that the lanes of a warp (consecutive cells) read consecutive words.
+    bool consecutive = true;
+    for (int c = 0; c < p->M3 && consecutive; ++c)
+        for (size_t t = 1; t < cells[c].size(); ++t)
+            if (cells[c][t].first != cells[c][0].first + (int)t) consecutive = false;
+    if (consecutive) {
+        std::vector<int2> zrange(p->M3);
+        std::vector<float> zwt((size_t)std::max(zmax, 1) * p->M3, 0.f);
+        for (int c = 0; c < p->M3; ++c) {
+            zrange[c] = make_int2(cells[c].empty() ? 0 : cells[c][0].first, (int)cells[c].size());
+            for (size_t t = 0; t < cells[c].size(); ++t) zwt[t * p->M3 + c] = cells[c][t].second;
+        }
+        if ((rc = upload(p, &p->d_zrange, zrange, "x3 table ranges"))) return rc;
+        if ((rc = upload(p, &p->d_zwt, zwt, "x3 table weights by tap"))) return rc;
+    }
     if ((rc = upload(p, &p->d_zoff, zoff, "x3 table offsets"))) return rc;
     if ((rc = upload(p, &p->d_zl, zl, "x3 table planes"))) return rc;
     if ((rc = upload(p, &p->d_zw, zw, "x3 table weights"))) return rc;
