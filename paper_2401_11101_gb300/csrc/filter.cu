@@ -149,6 +149,12 @@ __device__ __forceinline__ void fft_warp(float2* x, const float2* __restrict__ t
     else fft512_warp(x, tw, s, lane);
 }
 
+// Pitch of the three decimated buffers of a row pair: 11 (mod 16) slots, so
+// that a half-warp's accesses to z[j] .. z[j + 15] (slots (j % 3) LB + j / 3)
+// fall on 16 different bank pairs (with LB = 0 (mod 16), three consecutive j
+// shared one).
+__host__ __device__ constexpr int pitch3(int n) { return n + ((11 - n) % 16 + 16) % 16; }
+
 // barrier of the 96 threads (three warps) of sequence `seq` of a block
 __device__ __forceinline__ void seq_sync(int seq) {
     asm volatile("bar.sync %0, 96;" ::"r"(seq + 1) : "memory");
@@ -219,12 +225,13 @@ __global__ void __launch_bounds__(384) k_filter3(const Tin* __restrict__ d, floa
     const long rA = row0 + 2 * ((long)blockIdx.x * (blockDim.x / 96) + seq);
     if (rA >= row1) return;                       // the whole sequence leaves: no barrier waits on it
     const bool hasB = rA + 1 < row1;
-    float2* buf = sm + (size_t)seq * 3 * N;
-    load_rows3(d, buf, N, N, rA, hasB, W, 0, t96);
+    constexpr int LB = pitch3(N);
+    float2* buf = sm + (size_t)seq * 3 * LB;
+    load_rows3(d, buf, LB, N, rA, hasB, W, 0, t96);
     seq_sync(seq);
-    filter_rows3<N>(buf, N, twN, tw3N, filt, t96, lane, seq);
+    filter_rows3<N>(buf, LB, twN, tw3N, filt, t96, lane, seq);
     for (int j = t96; j < W; j += 96) {
-        const float2 v = buf[(j % 3) * N + j / 3];
+        const float2 v = buf[(j % 3) * LB + j / 3];
         q[(size_t)rA * W + j] = v.x;
         if (hasB) q[(size_t)(rA + 1) * W + j] = v.y;
     }
@@ -245,7 +252,7 @@ __global__ void __launch_bounds__(384, 2) k_rowfft3(const Tin* __restrict__ d, f
                                                  const float2* __restrict__ twNF, const float2* __restrict__ tw3NF,
                                                  const float2* __restrict__ phu) {
     extern __shared__ float2 sm[];
-    constexpr int LB = (N > NF) ? N : NF;
+    constexpr int LB = pitch3((N > NF) ? N : NF);
     const int seq = threadIdx.x / 96, t96 = threadIdx.x % 96, lane = threadIdx.x & 31, w3 = t96 >> 5;
     const long rA = row0 + 2 * ((long)blockIdx.x * (blockDim.x / 96) + seq);
     if (rA >= row1) return;
@@ -318,7 +325,7 @@ int filter_typed(lamino_plan_t p, const Tin* d, float* q, int kind, cudaStream_t
     if (p->fWp3.n == 512 || p->fWp3.n == 256) {
         // three one-warp transforms per row pair, four row pairs per block
         const int N = p->fWp3.n;
-        const size_t smem = sizeof(float2) * 3 * N * 4;
+        const size_t smem = sizeof(float2) * 3 * pitch3(N) * 4;
         dim3 grid((unsigned)((npairs + 3) / 4));
         ProfScope prof(p, "filter", s);
         if (N == 512) {
@@ -379,7 +386,7 @@ int rowfft3_launch(lamino_plan_t p, const Tin* d, float2* R, const float* filt, 
                    long row0, long row1) {
     long npairs = (row1 - row0 + 1) / 2;
     if (npairs <= 0) return LAMINO_OK;
-    constexpr int LB = (N > NF) ? N : NF;
+    constexpr int LB = pitch3((N > NF) ? N : NF);
     const size_t smem = sizeof(float2) * 3 * LB * 4;
     dim3 grid((unsigned)((npairs + 3) / 4));
     auto kern = k_rowfft3<N, NF, Tin>;
